@@ -1,0 +1,370 @@
+"""Benchmark: MLUPS and HBM-roofline fraction of the fused fluctuating-LB step.
+
+Default workload: D3Q19 Taylor-Green vortex, 256^3 periodic, Re = 100,
+Wi = 1, beta = 0.5, u0 = 0.02, FP32 storage and arithmetic, fused kernel.
+One step = one fused collide-stream-stress launch over all 16.8 M sites.
+The state (18 GB) is far larger than L2, so no L2 flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an
+independent replica of the workload on its own GPU (the method's single
+grid does not shard here) and `value` counts the updates of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline per form at <=1e-3 rel-L2 vs FP64 oracle"
+UNIT = "MLUPS"
+WORKLOAD = dict(lattice="D3Q19", n=256, Re=100.0, Wi=1.0, beta=0.5, U0=0.02)
+KERNEL_SOURCES = ["paper_2506_13072_gb300/csrc/fvlb_kernels.cuh",
+                  "paper_2506_13072_gb300/csrc/fvlb_lattice.cuh",
+                  "paper_2506_13072_gb300/csrc/fvlb_launch.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_record(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, valid only while
+    the kernel sources are unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    r = rec.get(kernel_key)
+    if not r or r.get("kernel_hash") != kernel_hash():
+        return None
+    return r
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fvlb_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = sorted(v for v in (num(r[1]) for r in rows) if v is not None)
+        mx = max((v for v in (num(r[2]) for r in rows) if v is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        pw = [v for v in (num(r[3]) for r in rows) if v is not None]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+def tgv_problem(n):
+    from paper_2506_13072_gb300 import workloads as W
+
+    w = WORKLOAD
+    return W.taylor_green_3d(n=n, U0=w["U0"], Re=w["Re"], Wi=w["Wi"], beta=w["beta"])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle, timed on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def oracle_rate(seconds: float = 12.0, n: int = 32):
+    """The FP64 oracle (single thread) on a 32^3 Taylor-Green box with the
+    same physics; returns (MLUPS, steps, sites)."""
+    import oracle as O
+
+    pr = tgv_problem(n)
+    o = O.Oracle(pr.lattice, **pr.oracle_kwargs())
+    o.init(u=pr.u0, p=pr.p0, A=pr.A0)
+    o.step(1)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return pr.sites * steps / dt / 1e6, steps, pr.sites
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_step = []
+    import oracle as O
+
+    pr = tgv_problem(32)
+    o = O.Oracle(pr.lattice, **pr.oracle_kwargs())
+    o.init(u=pr.u0, p=pr.p0, A=pr.A0)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s0 = time.perf_counter()
+        o.step(1)
+        per_step.append(time.perf_counter() - s0)
+    dt = time.perf_counter() - t0
+    value = pr.sites * args.steps / dt / 1e6
+    sample = f"FP64 CPU oracle, single thread, D3Q19 Taylor-Green 32^3 (same Re, Wi, beta), {args.steps} steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict("oracle sample 32^3"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(note=""):
+    w = WORKLOAD
+    return {"workload": f"D3Q19 Taylor-Green vortex {w['n']}^3 periodic, Re={w['Re']:g}, "
+                        f"Wi={w['Wi']:g}, beta={w['beta']:g}, u0={w['U0']:g}, FP32 fused step",
+            "lattice": w["lattice"], "grid": [w["n"]] * 3, "precision": "fp32",
+            "kernel": "fused", "l2": "state 18 GB >> 129 MB L2; no flush needed",
+            "parallelism": "replicas", "note": note}
+
+
+# ---------------------------------------------------------------------------
+# GPU
+# ---------------------------------------------------------------------------
+
+def time_steps(sim, steps, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def form_rate(F, pr, precision, steps, warmup, stream, kernel=0):
+    import torch
+
+    s = F.Simulation.from_problem(pr, precision=precision, kernel=kernel, stream=stream)
+    s.init_fields(pr.u0, pr.p0, pr.A0)
+    s.step(warmup)
+    torch.cuda.synchronize()
+    dt = time_steps(s, steps, stream)
+    bpu = s.bytes_per_update()
+    s.close()
+    mlups = pr.sites * steps / dt / 1e6
+    return {"mlups": round(mlups, 1), "gbs_algorithmic": round(bpu * pr.sites * steps / dt / 1e9, 1),
+            "bytes_per_update": bpu, "ms_per_step": round(1e3 * dt / steps, 4)}
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2506_13072_gb300 import fvlb as F
+    from paper_2506_13072_gb300 import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    F.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    pr = tgv_problem(WORKLOAD["n"])
+    sim = F.Simulation.from_problem(pr, precision=F.FVLB_FP32, kernel=F.FVLB_KERNEL_FUSED,
+                                    stream=stream)
+    sim.init_fields(pr.u0, pr.p0, pr.A0)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        dt = time_steps(sim, args.steps, stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+        dist.barrier()
+    diag = sim.reduce(check_finite=False)
+    bpu = sim.bytes_per_update()
+    sim.close()
+
+    sites = pr.sites
+    value = sites * args.steps * world / dt / 1e6
+    launch_s = dt / args.steps                 # one fused launch per step
+    achieved = bpu * sites / launch_s / 1e9    # GB/s, algorithmic bytes
+    peaks, which = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    tr = traffic_record("tgv256_fp32_fused")
+
+    # end to end through the public API, host buffers: upload of the initial
+    # fields, K steps, download of the velocity field, all inside the region
+    u0 = np.ascontiguousarray(pr.u0)
+    p0 = np.ascontiguousarray(pr.p0)
+    A0 = np.ascontiguousarray(F.full_to_compact(np.broadcast_to(np.eye(3), pr.shape + (3, 3))))
+    e2e_steps = args.steps
+    sim = F.Simulation.from_problem(pr, precision=F.FVLB_FP32, stream=stream)
+    sim.init_fields(u0, p0, A0)
+    sim.step(2)
+    out = np.empty(sites * 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.init_fields(u0, p0, A0)
+    sim.step(e2e_steps)
+    sim.fields(F.FVLB_FIELD_U, out)
+    e2e_dt = time.perf_counter() - t0
+    sim.close()
+    h2d = (u0.nbytes + p0.nbytes + A0.nbytes) / e2e_steps
+    d2h = out.nbytes / e2e_steps
+
+    forms = {}
+    if not args.no_forms and rank == 0:
+        K = max(5, min(args.steps, 20))
+        for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("bf16_dev", F.FVLB_BF16_DEV),
+                           ("fp64", F.FVLB_FP64)):
+            forms[f"d3q19_256^3_{name}"] = form_rate(F, pr, prec, K, 2, stream)
+            torch.cuda.empty_cache()
+        pr2 = W.four_roll(n=2048, Wi=0.5, beta=0.5)
+        for name, prec in (("fp32", F.FVLB_FP32), ("fp16_dev", F.FVLB_FP16_DEV)):
+            forms[f"d2q9_2048^2_four_roll_{name}"] = form_rate(F, pr2, prec, K, 2, stream)
+        forms["d3q19_256^3_fp32_split"] = form_rate(F, pr, F.FVLB_FP32, K, 2, stream, kernel=1)
+        for k, v in forms.items():
+            v["frac_of_hbm_peak"] = round(v["gbs_algorithmic"] / peak, 3)
+        torch.cuda.synchronize()
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        rate, steps, n = oracle_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 CPU oracle, single thread, D3Q19 Taylor-Green 32^3 "
+                         f"({n} sites, same Re/Wi/beta), {steps} steps in ~12 s"}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Taylor-Green initial field of Sec. 3.4)",
+        "config": config_dict(),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                     "algorithmic_bytes_per_launch": bpu * sites,
+                     "bytes_per_update": bpu, "peak_source": f"{which} hbm_gbs (copy)",
+                     "kernel": "k_step_fused<D3Q19,float,32,8>"},
+        "e2e": {"value": round(sites * e2e_steps / e2e_dt / 1e6, 1), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "fvlb_init_fields from host + K steps + fvlb_fields(U) to host"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "diagnostics": {"KE": diag["KE"], "PE": diag["PE"], "nonfinite": diag["nonfinite"]},
+        "forms": forms,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * fvlb.h -- C ABI of the GB300 (sm_103a) library for the fluctuating lattice
+ * Boltzmann method for Oldroyd-B fluids of Wang, Liu, Wang, Yu and Ji
+ * (arXiv 2506.13072).
+ *
+ * One handle is one simulation on one GPU: a D2Q9 or D3Q19 grid of
+ * nx * ny * nz sites carrying the flow populations f_i (Sec. 2.2, evolution
+ * equation with the polymer-stress fluctuation term f^B and Guo forcing),
+ * the conformation-tensor populations h_{ab,i} (Sec. 2.3) and the previous
+ * step's stress source chi (for the 0.5 dt^2 d(chi_i)/dt term).  One call of
+ * fvlb_step advances every site by one fused collide-and-stream update.
+ *
+ * Conventions shared by every entry point
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3, rho_0 = 1.
+ *   - Sites are ordered x fastest: s = (z * ny + y) * nx + x (nz = 1 in 2D).
+ *   - Host field arrays are FP64, site-major, components last:
+ *       velocity u        [N][D]
+ *       pressure p        [N]
+ *       conformation A    [N][C]  symmetric components,
+ *       polymer stress    [N][C]  C = 3 in 2D (xx, xy, yy),
+ *                                 C = 6 in 3D (xx, yy, zz, xy, xz, yz).
+ *   - Ownership: the caller owns every host buffer it passes; the library
+ *     owns all device memory of a handle and never returns device pointers.
+ *   - Errors: every entry point returns an int status (FVLB_OK = 0 or a
+ *     negative FVLB_E* code); no C++ exception crosses the ABI.  A failed
+ *     call leaves the simulation state unchanged unless stated otherwise.
+ *     fvlb_last_error gives a one-line description.
+ *   - Threading: a handle is not thread-safe; distinct handles are
+ *     independent.  All GPU work of a handle runs on its stream, in order.
+ */
+#ifndef FVLB_H
+#define FVLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fvlb_s *fvlb_t; /* opaque simulation handle */
+
+/* Lattices: D2Q9 (Sec. 2.2 c_i matrix and weights), D3Q19 (Appendix A c_i
+ * matrix; weights 1/3, 1/18, 1/36). */
+enum { FVLB_D2Q9 = 9, FVLB_D3Q19 = 19 };
+
+/* Status codes. */
+enum {
+  FVLB_OK = 0,
+  FVLB_EINVAL = -1,    /* invalid argument; nothing was changed */
+  FVLB_ENOMEM = -2,    /* a device allocation failed */
+  FVLB_ECUDA = -3,     /* a CUDA call failed */
+  FVLB_EUNSTABLE = -4, /* the diagnostics found a non-finite value */
+  FVLB_ETIMEOUT = -5,  /* a bounded device wait ran out */
+  FVLB_ESTATE = -6     /* call not allowed in the handle's current state */
+};
+
+/* Body force F(x, t) entering u = sum c_i f_i + F/2 and the Guo term F_i
+ * (Sec. 2.2).  Positions are node indices, t is the step count.
+ *   NONE       F = 0
+ *   CONST      F = F0                                       (Sec. 3.2)
+ *   FOUR_ROLL  F = F0[0] (sin kx cos ky, -cos kx sin ky, 0) (Sec. 3.1)
+ *   COSINE     F = F0 cos(omega t)                          (Sec. 3.3) */
+enum {
+  FVLB_FORCE_NONE = 0,
+  FVLB_FORCE_CONST = 1,
+  FVLB_FORCE_FOUR_ROLL = 2,
+  FVLB_FORCE_COSINE = 3
+};
+
+typedef struct {
+  int kind;     /* FVLB_FORCE_* */
+  double F0[3]; /* amplitude vector, lattice units */
+  double k;     /* FOUR_ROLL wavenumber (2 pi / n for n periodic nodes) */
+  double omega; /* COSINE angular frequency per step */
+} fvlb_force;
+
+/* Storage precision of the populations (set before the first state-using
+ * call).  Every form stores f (whose rest equilibrium is 0) and
+ * h_ab,i - w_i delta_ab (the deviation from the rest equilibrium A = I).
+ * FP64 and FP32 compute in that precision.  The 16-bit forms compute in
+ * FP32 and keep chi in FP32; FP16_DEV and BF16_DEV round to nearest when
+ * storing, FP16_DEV_SR and BF16_DEV_SR round stochastically (unbiased, with
+ * random bits from a counter-based hash of site and step, so runs are
+ * reproducible). */
+enum {
+  FVLB_FP64 = 0,
+  FVLB_FP32 = 1,
+  FVLB_FP16_DEV = 2,
+  FVLB_BF16_DEV = 3,
+  FVLB_FP16_DEV_SR = 4,
+  FVLB_BF16_DEV_SR = 5
+};
+
+/* Kernel variant: FUSED is one launch per step (the velocity gradient comes
+ * from a shared-memory ring of velocity planes); SPLIT is two launches per
+ * step (velocity field to a device buffer, then collide-and-stream). */
+enum { FVLB_KERNEL_FUSED = 0, FVLB_KERNEL_SPLIT = 1 };
+
+/* Fields for fvlb_fields. */
+enum {
+  FVLB_FIELD_U = 0,    /* u = sum_{i!=0} c_i f_i + F/2 (Sec. 2.2)            */
+  FVLB_FIELD_P = 1,    /* p of Sec. 2.2 / Appendix B                         */
+  FVLB_FIELD_A = 2,    /* A_ab = sum_i h_ab,i (Sec. 2.3)                     */
+  FVLB_FIELD_TAU_P = 3 /* tau_p = (eta_p / lambda)(A - I) (Sec. 2.1)         */
+};
+
+/* Device-memory hooks.  alloc(bytes, ctx) must return device memory aligned
+ * to at least 256 bytes on the device that is current, or NULL; free(ptr,
+ * ctx) releases it.  The hooks are process-wide and are captured by each
+ * handle when it first allocates, so changing them later does not affect
+ * existing handles.  Passing NULL for both restores cudaMalloc / cudaFree.
+ * Returns FVLB_EINVAL if exactly one of the two is NULL. */
+typedef void *(*fvlb_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*fvlb_free_fn)(void *ptr, void *ctx);
+int fvlb_set_allocator(fvlb_alloc_fn alloc_fn, fvlb_free_fn free_fn, void *ctx);
+
+/* Create a simulation on the current CUDA device.
+ *   lattice   FVLB_D2Q9 or FVLB_D3Q19
+ *   nx,ny,nz  grid size, each >= 1 (nz is ignored and taken as 1 in 2D)
+ *   tau_s     flow relaxation time tau_f = nu_s / c_s^2 + 1/2 (Sec. 2.2);
+ *             must be > 0.5
+ *   eta_p     polymer viscosity mu_p = nu_p (rho_0 = 1), >= 0 (Sec. 2.1)
+ *   lambda    polymer relaxation time, > 0 (Sec. 2.1)
+ *   force     body force, or NULL for none (copied)
+ * The stress relaxation time is tau_h = 0.501 (Sec. 3).  No device memory
+ * is allocated here: the state is allocated, and set to rest (u = 0, p = 0,
+ * A = I) unless fvlb_init_fields was called, by the first call that needs
+ * it.  Defaults: no walls (fully periodic), FVLB_FP64, FVLB_KERNEL_FUSED,
+ * the legacy default stream.  On error *out is set to NULL. */
+int fvlb_create(fvlb_t *out, int lattice, int nx, int ny, int nz,
+                double tau_s, double eta_p, double lambda,
+                const fvlb_force *force);
+
+/* Halfway bounce-back walls: bit a of axis_mask puts a wall on both ends of
+ * axis a (0 = x, 1 = y, 2 = z), at distance 1/2 outside the first and last
+ * nodes, for both f and h; other axes are periodic.  A walled axis needs
+ * at least 2 nodes.  FVLB_ESTATE once the state is allocated. */
+int fvlb_set_walls(fvlb_t h, unsigned axis_mask);
+
+/* Storage precision (FVLB_FP64 ...); FVLB_ESTATE once the state is
+ * allocated. */
+int fvlb_set_precision(fvlb_t h, int storage);
+
+/* Kernel variant (FVLB_KERNEL_FUSED or FVLB_KERNEL_SPLIT); may be changed
+ * at any time, both give the same results up to rounding order. */
+int fvlb_set_kernel(fvlb_t h, int variant);
+
+/* CUDA stream (a cudaStream_t, or NULL for the legacy default stream) on
+ * which all later GPU work of the handle is enqueued. */
+int fvlb_set_stream(fvlb_t h, void *stream);
+
+/* Initial state (Sec. 2.2 / 2.3 equilibria): f = f^eq(p0, u0),
+ * h_ab,i = w_i A0_ab (1 + c_i.u0 / c_s^2), chi of the previous step unset
+ * (the first step's d(chi)/dt correction is 0), t = 0.  u0 [N][D], p0 [N],
+ * A0 [N][C] are host FP64 arrays; NULL means u0 = 0, p0 = 0, A0 = I.
+ * Allocates the state if needed.  Returns after the upload completed. */
+int fvlb_init_fields(fvlb_t h, const double *u0, const double *p0,
+                     const double *A0);
+
+/* Enqueue n >= 0 time steps on the handle's stream and return without
+ * waiting.  Each step evaluates the force at the current t, then t += 1. */
+int fvlb_step(fvlb_t h, long n);
+
+/* Copy one field of the current state into host_out (FP64, layouts above),
+ * synchronising the handle's stream.  count is the number of doubles the
+ * buffer holds; if it is smaller than N * components, FVLB_EINVAL is
+ * returned and nothing is written. */
+int fvlb_fields(fvlb_t h, int which, double *host_out, size_t count);
+
+/* FP64 diagnostics of the current state, reduced on the GPU in a fixed
+ * order (deterministic), synchronising the handle's stream:
+ *   out[0]   sum_x sum_i f_i                      (mass drift; 0 at rest)
+ *   out[1..3] sum_x sum_i c_i f_i                 (population momentum)
+ *   out[4]   KE = (1/M) sum_x |u|^2 / 2           (Sec. 3.4)
+ *   out[5]   PE = (1/M) sum_x tr(tau_p) / 2       (Sec. 3.4)
+ *   out[6]   number of sites with a non-finite f, h or u
+ *   out[7]   max_x |u|
+ * Returns FVLB_EUNSTABLE (with out filled) if out[6] > 0. */
+int fvlb_reduce(fvlb_t h, double out[8]);
+
+/* Wait for all GPU work of the handle. */
+int fvlb_synchronize(fvlb_t h);
+
+/* Current step count. */
+int fvlb_get_time(fvlb_t h, long *t);
+
+/* Checkpoint / resume: the raw state (populations, previous chi, step
+ * count and first-step flag) as an opaque byte image of fvlb_state_size
+ * bytes, valid for a handle with the same lattice, grid and precision.
+ * fvlb_load_state returns FVLB_EINVAL on a size or header mismatch. */
+int fvlb_state_size(fvlb_t h, size_t *bytes);
+int fvlb_save_state(fvlb_t h, void *host_buf, size_t bytes);
+int fvlb_load_state(fvlb_t h, const void *host_buf, size_t bytes);
+
+/* Bytes of HBM the step kernel moves per lattice update by construction
+ * (each population and chi read once and written once), for roofline
+ * accounting: 2 (Q + C Q) s + 2 C s_chi with s the storage size. */
+int fvlb_bytes_per_update(fvlb_t h, double *bytes);
+
+/* Last error message of the handle, or of the last failed fvlb_create /
+ * fvlb_set_allocator if h is NULL.  Never NULL. */
+const char *fvlb_last_error(fvlb_t h);
+
+/* Release the handle and its device memory (after waiting for its stream).
+ * NULL-safe. */
+int fvlb_destroy(fvlb_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVLB_H */

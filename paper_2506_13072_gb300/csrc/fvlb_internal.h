@@ -1,0 +1,65 @@
+// fvlb_internal.h -- host-side descriptors shared by the C-ABI layer and the
+// per-lattice kernel launchers.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace fvlb {
+
+enum Storage { kFP64 = 0, kFP32 = 1, kFP16Dev = 2, kBF16Dev = 3, kFP16DevSR = 4, kBF16DevSR = 5 };
+
+// Precision-agnostic description of one launch; the launcher converts the
+// physics to the working precision of the storage type.
+struct StepDesc {
+  int nx, ny, nz, walls;
+  long long N, pitch;
+  int storage;
+  int variant;          // 0 fused, 1 split
+  const void* f_in;
+  void* f_out;
+  const void* h_in;
+  void* h_out;
+  void* chi;
+  void* ubuf;           // split variant: D * pitch working-precision values
+  double tau_f, tau_h, eta_p, lambda;
+  int four_roll;
+  double Fv[3];         // uniform force of this step (CONST / COSINE)
+  double amp;           // FOUR_ROLL amplitude
+  const void* tables;   // FOUR_ROLL: sx[nx], cx[nx], sy[ny], cy[ny] in working precision
+  int first;
+  long long step;       // step count t of this launch
+  int sms;
+  cudaStream_t stream;
+};
+
+struct InitDesc {
+  int nx, ny, nz;
+  long long N, pitch;
+  int storage;
+  void* f;
+  void* h;
+  void* chi;
+  const double* u0;
+  const double* p0;
+  const double* A0;
+  int sms;
+  cudaStream_t stream;
+};
+
+// Per-lattice launchers (one translation unit per lattice).
+cudaError_t step_d2q9(const StepDesc& d);
+cudaError_t step_d3q19(const StepDesc& d);
+cudaError_t init_d2q9(const InitDesc& d);
+cudaError_t init_d3q19(const InitDesc& d);
+// fields: which as in fvlb.h; out is a device FP64 buffer
+cudaError_t fields_d2q9(const StepDesc& d, int which, double* out);
+cudaError_t fields_d3q19(const StepDesc& d, int which, double* out);
+// diagnostics: part has room for reduce_parts(N) * 8 doubles, out for 8
+int reduce_parts(long long N);
+cudaError_t reduce_d2q9(const StepDesc& d, double* part, double* out);
+cudaError_t reduce_d3q19(const StepDesc& d, double* part, double* out);
+cudaError_t reduce_finalize(const double* part, int nparts, long long N, double* out,
+                            cudaStream_t stream);
+
+}  // namespace fvlb

@@ -1,0 +1,623 @@
+// fvlb_kernels.cuh -- CUDA kernels of one fluctuating-LB time step
+// (arXiv 2506.13072, Sec. 2.2 flow LB with f^B and Guo forcing, Sec. 2.3
+// conformation LB), plus initialisation, field extraction and the FP64
+// diagnostics reduction.
+//
+// Data layout in HBM (structure of arrays, x fastest, each array padded to
+// `pitch` elements):  f[Q][pitch], h[C][Q][pitch], chi[C][pitch].  The state
+// is double-buffered (f and h read from one buffer, written to the other);
+// chi is read and rewritten in place by its own site only.
+//
+// A step is "collide, then push": the site reads its own populations
+// (coalesced, unshifted), collides, and writes population i to the
+// neighbour x + c_i of the other buffer (or, through a halfway-bounce-back
+// wall, to its own node in the opposite direction).  The velocity gradient
+// in chi needs the same-step velocity of the 2 (2D) or 6 (3D) nearest
+// neighbours, which with push streaming are one node away, so a one-node
+// velocity halo suffices.
+#pragma once
+
+#include "fvlb_lattice.cuh"
+
+namespace fvlb {
+
+template <class S>
+using RT = typename Store<S>::R;
+
+// Make a pointer opaque to the compiler at this point of the program.  Used
+// to stop the 114 population addresses of a D3Q19 site from being computed
+// once and kept live (in registers) between the two reads of the stress
+// populations, which would cap the number of resident warps.
+template <class T>
+__device__ __forceinline__ T* opaque(T* p) {
+  asm volatile("" : "+l"(p));
+  return p;
+}
+
+// load f_i(s)
+template <class L, class S>
+__device__ __forceinline__ void load_f(const S* __restrict__ f, long long pitch,
+                                       long long s, RT<S> (&fv)[L::Q]) {
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) fv[i] = Store<S>::ld(f + i * pitch + s);
+}
+
+// Stress populations are held as deviations from the rest equilibrium,
+// h'_{k,i} = h_{k,i} - w_i delta_k (delta_k = 1 on diagonal components), in
+// every storage precision: the conformation then enters as A - I = sum_i h'
+// without the cancellation of summing h ~ w_i A and subtracting I.
+template <class L, class S>
+__device__ __forceinline__ RT<S> load_h(const S* __restrict__ h, long long pitch,
+                                        long long s, int k, int i) {
+  return Store<S>::ld(h + (long long)(k * L::Q + i) * pitch + s);
+}
+
+// second read of a stress population within one site update (served by L2);
+// hs points at the site's first population
+template <class L, class S>
+__device__ __forceinline__ RT<S> reload_h(const S* hs, long long pitch, int k, int i) {
+  return Store<S>::ld_l2(hs + (long long)(k * L::Q + i) * pitch);
+}
+
+template <class L, class S>
+__device__ __forceinline__ void store_h(S* __restrict__ h, long long pitch,
+                                        long long s, int k, int i, RT<S> v, uint32_t r) {
+  Store<S>::st(h + (long long)(k * L::Q + i) * pitch + s, v, r);
+}
+
+template <class L>
+__host__ __device__ constexpr bool diag(int k) {
+  return L::ca(k) == L::cb(k);
+}
+
+// Streaming destination of population i leaving (x, y, z) (node s):
+// periodic wrap, or halfway bounce-back to the same node, opposite direction.
+template <class L>
+__device__ __forceinline__ long long push_dest(const Grid& g, int i, int x, int y,
+                                               int z, long long s, int& j) {
+  int xd = x + L::cx(i), yd = y + L::cy(i), zd = z + L::cz(i);
+  bool bb = false;
+  if (L::cx(i) != 0 && (xd < 0 || xd >= g.nx)) {
+    if (g.walls & 1) bb = true;
+    else xd = xd < 0 ? xd + g.nx : xd - g.nx;
+  }
+  if (L::cy(i) != 0 && (yd < 0 || yd >= g.ny)) {
+    if (g.walls & 2) bb = true;
+    else yd = yd < 0 ? yd + g.ny : yd - g.ny;
+  }
+  if (L::D == 3 && L::cz(i) != 0 && (zd < 0 || zd >= g.nz)) {
+    if (g.walls & 4) bb = true;
+    else zd = zd < 0 ? zd + g.nz : zd - g.nz;
+  }
+  if (bb) {
+    j = L::opp(i);
+    return s;
+  }
+  j = i;
+  return ((long long)zd * g.ny + yd) * g.nx + xd;
+}
+
+// p = c_s^2 / (1 - w_0) [sum_{i!=0} f_i + s_0(u) + tau_f F_0 + tau_f f^B_0]
+// (Sec. 2.2, Appendix B) with F_0 = -3 w_0 (1 - 1/(2 tau_f)) F.u and
+// s_0 = -1.5 w_0 |u|^2.
+template <class L, class R>
+__device__ __forceinline__ R pressure(const Phys<R>& ph, const R (&f)[L::Q],
+                                      const R (&u)[L::D], const R F[3], R fB0) {
+  R sum = R(0);
+#pragma unroll
+  for (int i = 1; i < L::Q; ++i) sum += f[i];
+  R uu = R(0), Fu = R(0);
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    uu += u[a] * u[a];
+    Fu += F[a] * u[a];
+  }
+  constexpr double w0 = L::w(0);
+  const R s0 = R(-1.5 * w0) * uu;
+  const R F0 = R(-3.0 * w0) * ph.kf * Fu;
+  return R(1.0 / (3.0 * (1.0 - w0))) * (sum + s0 + ph.tau_f * F0 + ph.tau_f * fB0);
+}
+
+// ---------------------------------------------------------------------------
+// Collide one site and push its populations.  u and gr (d_a u_b) are the
+// site's velocity and velocity gradient of this step; f its populations.
+// HOLD_H keeps all C*Q stress populations in registers (2D); otherwise the
+// conformation is summed in a first pass and each component re-read for its
+// collision (3D, where C*Q = 114).
+// ---------------------------------------------------------------------------
+template <class L, class S, bool HOLD_H>
+__device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& ph,
+                                             const Bufs<S>& b, long long s, int x,
+                                             int y, int z, const RT<S> (&u)[L::D],
+                                             const RT<S> (&gr)[L::D][L::D],
+                                             const RT<S> (&f)[L::Q], const RT<S> F[3]) {
+  using R = RT<S>;
+  using X = typename Store<S>::X;
+  constexpr int D = L::D, Q = L::Q, C = L::C;
+  const long long P = g.pitch;
+  // stochastic-rounding stream of this site and step (unused otherwise)
+  uint32_t rng = Store<S>::sr ? hash32((uint32_t)s * 0x9e3779b9u ^ hash32(ph.step)) : 0u;
+
+  // --- conformation A = I + sum_i h' (Sec. 2.3) --------------------------
+  R Ad[C];  // A - I
+  R hv[HOLD_H ? C : 1][HOLD_H ? Q : 1];
+#pragma unroll
+  for (int k = 0; k < C; ++k) {
+    // Q loads in flight per component: keeps the register footprint (and so
+    // the number of resident warps) bounded when the populations are re-read
+    // below instead of held.
+    const S* hk = HOLD_H ? b.h_in + s : opaque(b.h_in + s);
+    R a = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R v = Store<S>::ld(hk + (long long)(k * Q + i) * P);
+      if (HOLD_H) hv[HOLD_H ? k : 0][HOLD_H ? i : 0] = v;
+      a += v;
+    }
+    Ad[k] = a;
+  }
+  // --- flow collision inputs (Sec. 2.2) ------------------------------------
+  // f^B is linear in tau_p = (eta_p/lambda)(A - I): evaluate it on A - I with
+  // the factor eta_p / (lambda tau_f) folded in.
+  const R kB = ph.eta_over_lam * ph.inv_tau_f;
+  R uu = R(0), Fu = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    uu += u[a] * u[a];
+    Fu += F[a] * u[a];
+  }
+  const R fB0 = fB_dir<L, R>(0, Ad, kB);
+  const R p = pressure<L, R>(ph, f, u, F, fB0);
+
+  // --- stress source (Sec. 2.3) ---------------------------------------------
+  R src[C];
+  {
+    R A[C], chi[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) A[k] = Ad[k] + (diag<L>(k) ? R(1) : R(0));
+    chi_tensor<L, R>(A, Ad, gr, ph.inv_lam, chi);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      R old = R(b.chi[k * P + s]);
+      if (ph.first) old = chi[k];
+      b.chi[k * P + s] = X(chi[k]);
+      // chi_i + 0.5 (chi_i^n - chi_i^{n-1}) = phi_i (1.5 chi - 0.5 chi_old)
+      src[k] = R(1.5) * chi[k] - R(0.5) * old;
+    }
+  }
+
+  // --- collide and push, one direction at a time ----------------------------
+  // The destination of direction i is computed once and shared by f_i and
+  // the C stress populations h_{k,i}.
+  const S* hs = b.h_in + s;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (!HOLD_H && i % 3 == 0) hs = opaque(hs);
+    R cu = R(0), cF = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int c = cc<L>(i, a);
+      if (c == 1) { cu += u[a]; cF += F[a]; }
+      if (c == -1) { cu -= u[a]; cF -= F[a]; }
+    }
+    int j;
+    const long long d = push_dest<L>(g, i, x, y, z, s, j);
+    const R wi = R(L::w(i));
+
+    // flow: f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
+    const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
+    const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+    const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
+    const R fBi = fB_dir<L, R>(i, Ad, kB);
+    const R fpost = f[i] - (f[i] - feq) * ph.inv_tau_f + fBi + Fi;
+    Store<S>::st(b.f_out + j * P + d, fpost, Store<S>::sr ? lcg_next(rng) : 0u);
+
+    // stress: h* = h - (h - h^eq)/tau_h + phi_i src, phi_i = w_i [1 + (1 - 1/(2 tau_h)) c.u/c_s^2]
+    const R phi = wi * (R(1) + ph.kh * R(3) * cu);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const R hi = HOLD_H ? hv[HOLD_H ? k : 0][HOLD_H ? i : 0]
+                          : reload_h<L, S>(hs, P, k, i);
+      // h^eq - w_i delta_k = w_i [(A - I)_k + A_k c_i.u / c_s^2]
+      const R heq = wi * (Ad[k] + (Ad[k] + (diag<L>(k) ? R(1) : R(0))) * (R(3) * cu));
+      const R post = hi - (hi - heq) * ph.inv_tau_h + phi * src[k];
+      store_h<L, S>(b.h_out, P, d, k, j, post, Store<S>::sr ? lcg_next(rng) : 0u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused step: one launch per time step.
+//
+// A block owns a TX x TY tile of the plane orthogonal to the march axis
+// (2D: a run of TX nodes along x, TY = 1, marching along y; 3D: TX x TY in
+// x-y, marching along z) and a chunk of `mchunk` planes along the march
+// axis.  For each plane it first computes the velocity of the tile plus a
+// one-node halo into a three-plane shared-memory ring, then collides the
+// tile using central differences from the ring.  Velocities on halo nodes
+// are recomputed from their populations (read through L2) rather than
+// exchanged, so no block waits on another.
+// ---------------------------------------------------------------------------
+template <class L, class S, int TX, int TY, bool HOLD_H, int MINB>
+__global__ void __launch_bounds__(TX* TY, MINB)
+    k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
+  using R = RT<S>;
+  constexpr int D = L::D, Q = L::Q;
+  constexpr int NT = TX * TY;
+  constexpr int EX = TX + 2;
+  constexpr int EY = (D == 3) ? TY + 2 : 1;
+  constexpr int NE = EX * EY;
+  static_assert(D == 3 || TY == 1, "2D tiles are one row high");
+  __shared__ R ring[3][D][NE];
+
+  const int nx = g.nx, ny = g.ny;
+  const int nm = (D == 3) ? g.nz : g.ny;
+  const bool wall_x = g.walls & 1;
+  const bool wall_y = (D == 3) && ((g.walls >> 1) & 1);
+  const bool wall_m = (g.walls >> (D - 1)) & 1;
+  const int x0 = blockIdx.x * TX;
+  const int y0 = (D == 3) ? blockIdx.y * TY : 0;
+  const int m0 = blockIdx.z * mchunk;
+  const int m1 = min(m0 + mchunk, nm);
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x = x0 + tx;
+  const int y = (D == 3) ? y0 + ty : 0;
+  const bool active = (x < nx) && (D == 2 || y < ny);
+  const int e_own = (D == 3) ? (ty + 1) * EX + tx + 1 : tx + 1;
+  const long long P = g.pitch;
+
+  // Velocity of every extended-tile slot of plane m into ring slot r.  A
+  // thread owns at most NR slots; all their population loads are issued
+  // before any velocity is formed, so the halo slots cost no second
+  // round-trip to memory.
+  constexpr int NR = (NE + NT - 1) / NT;
+  auto fill = [&](int m, int r) {
+    if (m < 0 || m >= nm) {
+      if (wall_m) return;
+      m = (m + nm) % nm;
+    }
+    R fv[NR][Q];
+    bool ok[NR];
+    int gxs[NR], gys[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int e = tid + q * NT;
+      ok[q] = e < NE;
+      const int ex = e % EX, ey = e / EX;
+      int gx = x0 + ex - 1;
+      int gy = (D == 3) ? y0 + ey - 1 : 0;
+      if (gx < 0 || gx >= nx) {
+        if (wall_x) ok[q] = false;
+        else gx = ((gx % nx) + nx) % nx;
+      }
+      if (D == 3 && (gy < 0 || gy >= ny)) {
+        if (wall_y) ok[q] = false;
+        else gy = ((gy % ny) + ny) % ny;
+      }
+      gxs[q] = gx;
+      gys[q] = gy;
+      if (ok[q]) {
+        const long long s = (D == 3) ? ((long long)m * ny + gy) * nx + gx
+                                     : (long long)m * nx + gx;
+        load_f<L, S>(b.f_in, P, s, fv[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int e = tid + q * NT;
+      if (e >= NE) continue;
+      R u[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) u[a] = R(0);
+      if (ok[q]) {
+        R F[3];
+        body_force<L, R>(ph, gxs[q], D == 3 ? gys[q] : m, F);
+        velocity<L, R>(fv[q], F, u);
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) ring[r][a][e] = u[a];
+    }
+  };
+
+  fill(m0 - 1, 0);
+  fill(m0, 1);
+  for (int m = m0; m < m1; ++m) {
+    const int rm = (m - m0) % 3, rc = (m - m0 + 1) % 3, rp = (m - m0 + 2) % 3;
+    fill(m + 1, rp);
+    __syncthreads();
+    if (active) {
+      R u[D], gr[D][D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) u[a] = ring[rc][a][e_own];
+#pragma unroll
+      for (int bq = 0; bq < D; ++bq) {
+        const R uo = u[bq];
+        // x
+        {
+          const R up = ring[rc][bq][e_own + 1], um = ring[rc][bq][e_own - 1];
+          R d = R(0.5) * (up - um);
+          if (wall_x && x == 0) d = uo + up * R(1.0 / 3.0);
+          if (wall_x && x == nx - 1) d = -(uo + um * R(1.0 / 3.0));
+          gr[0][bq] = d;
+        }
+        if (D == 3) {
+          const R up = ring[rc][bq][e_own + EX], um = ring[rc][bq][e_own - EX];
+          R d = R(0.5) * (up - um);
+          if (wall_y && y == 0) d = uo + up * R(1.0 / 3.0);
+          if (wall_y && y == ny - 1) d = -(uo + um * R(1.0 / 3.0));
+          gr[1][bq] = d;
+        }
+        {
+          const R up = ring[rp][bq][e_own], um = ring[rm][bq][e_own];
+          R d = R(0.5) * (up - um);
+          if (wall_m && m == 0) d = uo + up * R(1.0 / 3.0);
+          if (wall_m && m == nm - 1) d = -(uo + um * R(1.0 / 3.0));
+          gr[D - 1][bq] = d;
+        }
+      }
+      const long long s = (D == 3) ? ((long long)m * ny + y) * nx + x : (long long)m * nx + x;
+      R fv[Q];
+      load_f<L, S>(b.f_in, P, s, fv);
+      R F[3];
+      body_force<L, R>(ph, x, D == 3 ? y : m, F);
+      if (D == 3) collide_site<L, S, HOLD_H>(g, ph, b, s, x, y, m, u, gr, fv, F);
+      else collide_site<L, S, HOLD_H>(g, ph, b, s, x, m, 0, u, gr, fv, F);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split step: velocity field to a device buffer, then collide-and-push with
+// the gradient read from that buffer.  One thread per site.
+// ---------------------------------------------------------------------------
+template <class L, class S>
+__global__ void k_velocity(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
+                           RT<S>* __restrict__ ubuf, long long N) {
+  using R = RT<S>;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(s % g.nx);
+    const int y = (int)((s / g.nx) % g.ny);
+    R fv[L::Q];
+    load_f<L, S>(f, g.pitch, s, fv);
+    R F[3];
+    body_force<L, R>(ph, x, y, F);
+    R u[L::D];
+    velocity<L, R>(fv, F, u);
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) ubuf[a * g.pitch + s] = u[a];
+  }
+}
+
+template <class L, class S, bool HOLD_H>
+__global__ void k_collide_split(Grid g, Phys<RT<S>> ph, Bufs<S> b,
+                                const RT<S>* __restrict__ ubuf, long long N) {
+  using R = RT<S>;
+  constexpr int D = L::D;
+  const long long P = g.pitch;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(s % g.nx);
+    const int y = (int)((s / g.nx) % g.ny);
+    const int z = (int)(s / ((long long)g.nx * g.ny));
+    const int p[3] = {x, y, z};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const long long stride[3] = {1, g.nx, (long long)g.nx * g.ny};
+    R u[D], gr[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = ubuf[a * P + s];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const bool wall = (g.walls >> a) & 1;
+      const long long sp = p[a] + 1 < n[a] ? s + stride[a] : s - (long long)(n[a] - 1) * stride[a];
+      const long long sm = p[a] > 0 ? s - stride[a] : s + (long long)(n[a] - 1) * stride[a];
+#pragma unroll
+      for (int bq = 0; bq < D; ++bq) {
+        const R up = ubuf[bq * P + sp], um = ubuf[bq * P + sm];
+        R d = R(0.5) * (up - um);
+        if (wall && p[a] == 0) d = u[bq] + up * R(1.0 / 3.0);
+        if (wall && p[a] == n[a] - 1) d = -(u[bq] + um * R(1.0 / 3.0));
+        gr[a][bq] = d;
+      }
+    }
+    R fv[L::Q];
+    load_f<L, S>(b.f_in, P, s, fv);
+    R F[3];
+    body_force<L, R>(ph, x, y, F);
+    collide_site<L, S, HOLD_H>(g, ph, b, s, x, y, z, u, gr, fv, F);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: f = f^eq(p0, u0), h = w_i A0 (1 + c_i.u0 / c_s^2), chi = 0.
+// u0 [N][D], p0 [N], A0 [N][C] in FP64 (each may be null: 0, 0, I).
+// ---------------------------------------------------------------------------
+template <class L, class S>
+__global__ void k_init(Grid g, S* __restrict__ f, S* __restrict__ h,
+                       typename Store<S>::X* __restrict__ chi,
+                       const double* __restrict__ u0, const double* __restrict__ p0,
+                       const double* __restrict__ A0, long long N) {
+  using R = RT<S>;
+  constexpr int D = L::D, Q = L::Q, C = L::C;
+  const long long P = g.pitch;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    R u[D], A[C];
+    R uu = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = u0 ? R(u0[s * D + a]) : R(0);
+      uu += u[a] * u[a];
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      A[k] = A0 ? R(A0[s * C + k]) : (L::ca(k) == L::cb(k) ? R(1) : R(0));
+    const R p = p0 ? R(p0[s]) : R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R cu = R(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) cu += R(cc<L>(i, a)) * u[a];
+      const R wi = R(L::w(i));
+      const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
+      Store<S>::st(f + i * P + s, lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu),
+                   0x80000000u);
+#pragma unroll
+      for (int k = 0; k < C; ++k)
+        store_h<L, S>(h, P, s, k, i,
+                      wi * ((A[k] - (diag<L>(k) ? R(1) : R(0))) + A[k] * (R(3) * cu)),
+                      0x80000000u);
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) chi[k * P + s] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic fields of the current state into a device FP64 buffer.
+// which: 0 u [N][D], 1 p [N], 2 A [N][C], 3 tau_p [N][C].
+// ---------------------------------------------------------------------------
+template <class L, class S>
+__global__ void k_fields(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
+                         const S* __restrict__ h, int which, double* __restrict__ out,
+                         long long N) {
+  using R = RT<S>;
+  constexpr int D = L::D, Q = L::Q, C = L::C;
+  const long long P = g.pitch;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(s % g.nx);
+    const int y = (int)((s / g.nx) % g.ny);
+    R fv[Q];
+    load_f<L, S>(f, P, s, fv);
+    R F[3];
+    body_force<L, R>(ph, x, y, F);
+    R u[D];
+    velocity<L, R>(fv, F, u);
+    if (which == 0) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) out[s * D + a] = double(u[a]);
+      continue;
+    }
+    R A[C], tp[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      R a = R(0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a += load_h<L, S>(h, P, s, k, i);
+      A[k] = a + (diag<L>(k) ? R(1) : R(0));
+      tp[k] = ph.eta_over_lam * a;
+    }
+    if (which == 1) {
+      const R fB0 = fB_dir<L, R>(0, tp, ph.inv_tau_f);
+      out[s] = double(pressure<L, R>(ph, fv, u, F, fB0));
+    } else if (which == 2) {
+#pragma unroll
+      for (int k = 0; k < C; ++k) out[s * C + k] = double(A[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < C; ++k) out[s * C + k] = double(tp[k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 diagnostics: per-block partial sums (fixed thread-to-site mapping and
+// a fixed shuffle tree), then one block reduces the partials in index order.
+// Deterministic for a given launch shape.
+// part: [gridDim.x][8] = {mass, Px, Py, Pz, sum |u|^2/2, sum tr(tau_p)/2,
+// non-finite count, max |u|}.
+// ---------------------------------------------------------------------------
+constexpr int kReduceThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <class L, class S>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_reduce_partial(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
+                     const S* __restrict__ h, double* __restrict__ part, long long N) {
+  using R = RT<S>;
+  constexpr int D = L::D, Q = L::Q, C = L::C;
+  const long long P = g.pitch;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(s % g.nx);
+    const int y = (int)((s / g.nx) % g.ny);
+    R fv[Q];
+    load_f<L, S>(f, P, s, fv);
+    bool bad = false;
+    double m = 0.0, mom[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double v = double(fv[i]);
+      bad |= !isfinite(v);
+      m += v;
+#pragma unroll
+      for (int a = 0; a < D; ++a) mom[a] += double(cc<L>(i, a)) * v;
+    }
+    R F[3];
+    body_force<L, R>(ph, x, y, F);
+    R u[D];
+    velocity<L, R>(fv, F, u);
+    double uu = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) uu += double(u[a]) * double(u[a]);
+    double tr = 0.0;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      if (L::ca(k) != L::cb(k)) {
+        // off-diagonal components only enter the finiteness check
+#pragma unroll
+        for (int i = 0; i < Q; ++i) bad |= !isfinite(double(load_h<L, S>(h, P, s, k, i)));
+        continue;
+      }
+      double a = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a += double(load_h<L, S>(h, P, s, k, i));
+      bad |= !isfinite(a);
+      tr += double(ph.eta_over_lam) * a;
+    }
+    bad |= !isfinite(uu);
+    acc[0] += m;
+    acc[1] += mom[0];
+    acc[2] += mom[1];
+    acc[3] += mom[2];
+    acc[4] += 0.5 * uu;
+    acc[5] += 0.5 * tr;
+    acc[6] += bad ? 1.0 : 0.0;
+    acc[7] = fmax(acc[7], isfinite(uu) ? sqrt(uu) : 0.0);
+  }
+  __shared__ double sm[kReduceThreads / 32][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double v = q == 7 ? warp_max(acc[q]) : warp_sum(acc[q]);
+    if (lane == 0) sm[wid][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int q = threadIdx.x;
+    double v = sm[0][q];
+    for (int w = 1; w < kReduceThreads / 32; ++w) v = q == 7 ? fmax(v, sm[w][q]) : v + sm[w][q];
+    part[blockIdx.x * 8 + q] = v;
+  }
+}
+
+// One block of kReduceThreads threads; out[8] as documented in fvlb.h.
+__global__ void __launch_bounds__(kReduceThreads)
+    k_reduce_final(const double* __restrict__ part, int nparts, long long nsites,
+                   double* __restrict__ out);
+
+}  // namespace fvlb

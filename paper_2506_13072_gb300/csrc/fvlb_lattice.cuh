@@ -1,0 +1,366 @@
+// fvlb_lattice.cuh -- lattice traits, storage traits and the per-site algebra
+// of the fluctuating lattice Boltzmann step (arXiv 2506.13072, Sec. 2.2-2.3),
+// written for the CUDA kernels of this library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace fvlb {
+
+// ---------------------------------------------------------------------------
+// Lattices.  Velocities in the paper's order: D2Q9 Sec. 2.2, D3Q19
+// Appendix A.  Weights: Sec. 2.2 (D2Q9); 1/3, 1/18, 1/36 (D3Q19, fixed by
+// 4th-order isotropy with c_s^2 = 1/3).  Symmetric tensor components are
+// stored compactly: 2D (xx, xy, yy), 3D (xx, yy, zz, xy, xz, yz).
+// All accessors are constexpr so that unrolled loops fold them away.
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+  static constexpr int D = 2, Q = 9, C = 3;
+  __host__ __device__ static constexpr int cx(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i < 5 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+  }
+  // compact component k -> (a, b)
+  __host__ __device__ static constexpr int ca(int k) { return k == 2 ? 1 : 0; }
+  __host__ __device__ static constexpr int cb(int k) { return k == 0 ? 0 : 1; }
+};
+
+struct D3Q19 {
+  static constexpr int D = 3, Q = 19, C = 6;
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+  // pairs (1,2) (3,4) ... (17,18) are opposite
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+  }
+  __host__ __device__ static constexpr int ca(int k) {
+    return k < 3 ? k : (k == 5 ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int cb(int k) {
+    return k < 3 ? k : (k == 3 ? 1 : 2);
+  }
+};
+
+template <class L>
+__host__ __device__ constexpr int cc(int i, int a) {
+  return a == 0 ? L::cx(i) : (a == 1 ? L::cy(i) : L::cz(i));
+}
+
+// compact index of (a, b)
+template <class L>
+__host__ __device__ constexpr int sym(int a, int b) {
+  if (L::D == 2) {
+    return (a == 0 && b == 0) ? 0 : ((a == 1 && b == 1) ? 2 : 1);
+  } else {
+    if (a == b) return a;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Storage traits: how a population is held in HBM and in which precision the
+// site arithmetic runs.  Every form holds f (whose rest equilibrium is 0) and
+// the stress populations as deviations from the rest equilibrium
+// (h_ab,i - w_i delta_ab).
+// ---------------------------------------------------------------------------
+// 16-bit re-read through L2 only; volatile so that it is not merged with the
+// first read of the same population.
+__device__ __forceinline__ unsigned short ld_l2_u16(const void* p) {
+  unsigned short v;
+  asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+
+template <class S>
+struct Store;
+
+template <>
+struct Store<double> {
+  using R = double;     // arithmetic
+  using X = double;     // chi of the previous step
+  __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
+  static constexpr bool sr = false;
+  __device__ static __forceinline__ void st(double* p, double v, uint32_t) { *p = v; }
+  __device__ static __forceinline__ double ld_l2(const double* p) {
+    double v;
+    asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+  }
+};
+
+template <>
+struct Store<float> {
+  using R = float;
+  using X = float;
+  __device__ static __forceinline__ float ld(const float* p) { return __ldg(p); }
+  static constexpr bool sr = false;
+  __device__ static __forceinline__ void st(float* p, float v, uint32_t) { *p = v; }
+  __device__ static __forceinline__ float ld_l2(const float* p) {
+    float v;
+    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+  }
+};
+
+template <>
+struct Store<__half> {
+  using R = float;
+  using X = float;
+  static constexpr bool sr = false;
+  __device__ static __forceinline__ float ld(const __half* p) {
+    return __half2float(__ldg(p));
+  }
+  __device__ static __forceinline__ void st(__half* p, float v, uint32_t) {
+    *p = __float2half_rn(v);
+  }
+  __device__ static __forceinline__ float ld_l2(const __half* p) {
+    return __half2float(__ushort_as_half(ld_l2_u16(p)));
+  }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+  using R = float;
+  using X = float;
+  static constexpr bool sr = false;
+  __device__ static __forceinline__ float ld(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+  }
+  __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, uint32_t) {
+    *p = __float2bfloat16_rn(v);
+  }
+  __device__ static __forceinline__ float ld_l2(const __nv_bfloat16* p) {
+    return __uint_as_float((uint32_t)ld_l2_u16(p) << 16);
+  }
+};
+
+// 16-bit forms with stochastic rounding: the value is rounded up or down to
+// a neighbouring representable number with probabilities proportional to
+// its distance from each, so the rounding error has zero mean and does not
+// accumulate coherently over steps.  Same bits in memory as __half /
+// __nv_bfloat16.
+struct half_sr {
+  unsigned short b;
+};
+struct bf16_sr {
+  unsigned short b;
+};
+
+template <>
+struct Store<half_sr> {
+  using R = float;
+  using X = float;
+  static constexpr bool sr = true;
+  __device__ static __forceinline__ float ld(const half_sr* p) {
+    return __half2float(__ushort_as_half(__ldg(&p->b)));
+  }
+  // r: 32 random bits.  Add r * ulp(|v|) in magnitude, then truncate.
+  __device__ static __forceinline__ void st(half_sr* p, float v, uint32_t r) {
+    const uint32_t bits = __float_as_uint(v);
+    int e = (int)((bits >> 23) & 0xffu) - 127;  // binade of |v|
+    e = e < -14 ? -14 : e;                      // half subnormals share one ulp
+    const float ulp = __uint_as_float((uint32_t)(e - 10 + 127) << 23);
+    const float jit = __uint2float_rz(r >> 8) * (1.0f / 16777216.0f) * ulp;
+    const float w = v + copysignf(jit, v);
+    p->b = __half_as_ushort(__float2half_rz(w));
+  }
+  __device__ static __forceinline__ float ld_l2(const half_sr* p) {
+    return __half2float(__ushort_as_half(ld_l2_u16(p)));
+  }
+};
+
+template <>
+struct Store<bf16_sr> {
+  using R = float;
+  using X = float;
+  static constexpr bool sr = true;
+  __device__ static __forceinline__ float ld(const bf16_sr* p) {
+    return __uint_as_float((uint32_t)__ldg(&p->b) << 16);
+  }
+  // add 16 random bits below the kept 16 and truncate (sign-magnitude, so the
+  // rounding is unbiased in magnitude and hence in value)
+  __device__ static __forceinline__ void st(bf16_sr* p, float v, uint32_t r) {
+    const uint32_t bits = __float_as_uint(v);
+    const uint32_t exp = bits & 0x7f800000u;
+    const uint32_t out = exp == 0x7f800000u ? bits : bits + (r >> 16);
+    p->b = (unsigned short)(out >> 16);
+  }
+  __device__ static __forceinline__ float ld_l2(const bf16_sr* p) {
+    return __uint_as_float((uint32_t)ld_l2_u16(p) << 16);
+  }
+};
+
+// Random bits for stochastic rounding: one counter-based hash per site and
+// step (the "lowbias32" integer hash of C. Wellons), then a 32-bit linear
+// congruential sequence (Numerical Recipes constants) whose high bits feed
+// one store each.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ uint32_t lcg_next(uint32_t& r) {
+  r = r * 1664525u + 1013904223u;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Launch-time description of a grid and of the physics of a step.
+// ---------------------------------------------------------------------------
+struct Grid {
+  int nx, ny, nz;     // nz = 1 in 2D
+  int walls;          // bit a: halfway bounce-back walls on axis a
+  long long pitch;    // elements between consecutive population arrays
+};
+
+template <class R>
+struct Phys {
+  R inv_tau_f;        // 1 / tau_f
+  R tau_f;
+  R inv_tau_h;        // 1 / tau_h
+  R kh;               // 1 - 1 / (2 tau_h)
+  R kf;               // 1 - 1 / (2 tau_f)
+  R eta_over_lam;     // eta_p / lambda
+  R inv_lam;          // 1 / lambda
+  int four_roll;      // 1: F = amp (sx cy, -cx sy); 0: F = Fv
+  R Fv[3];
+  R amp;
+  const R* sx;        // sin(k x), x < nx
+  const R* cxs;       // cos(k x)
+  const R* sy;        // sin(k y), y < ny
+  const R* cys;       // cos(k y)
+  int first;          // first step: chi of the previous step := chi
+  uint32_t step;      // step counter (stochastic-rounding stream)
+};
+
+template <class S>
+struct Bufs {
+  using X = typename Store<S>::X;
+  const S* __restrict__ f_in;
+  S* __restrict__ f_out;
+  const S* __restrict__ h_in;
+  S* __restrict__ h_out;
+  X* __restrict__ chi;  // [C][pitch], read and rewritten in place
+};
+
+// ---------------------------------------------------------------------------
+// Per-site algebra.
+// ---------------------------------------------------------------------------
+
+// Body force at (x, y); 3D forces do not depend on z.
+template <class L, class R>
+__device__ __forceinline__ void body_force(const Phys<R>& ph, int x, int y,
+                                           R F[3]) {
+  if (ph.four_roll) {
+    F[0] = ph.amp * __ldg(ph.sx + x) * __ldg(ph.cys + y);
+    F[1] = -ph.amp * __ldg(ph.cxs + x) * __ldg(ph.sy + y);
+    F[2] = R(0);
+  } else {
+    F[0] = ph.Fv[0];
+    F[1] = ph.Fv[1];
+    F[2] = ph.Fv[2];
+  }
+}
+
+// u = sum_{i != 0} c_i f_i + F / 2   (Sec. 2.2)
+template <class L, class R>
+__device__ __forceinline__ void velocity(const R (&f)[L::Q], const R F[3],
+                                         R (&u)[L::D]) {
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    R m = R(0);
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+      const int c = cc<L>(i, a);
+      if (c == 1) m += f[i];
+      else if (c == -1) m -= f[i];
+    }
+    u[a] = m + R(0.5) * F[a];
+  }
+}
+
+// f^B for a symmetric polymer stress (compact components t[C]).  This is
+// the least-norm solution of the three moment constraints of Sec. 2.2
+// (sum f^B = 0, sum c f^B = 0, sum c c f^B = -tau_p / tau_f), written per
+// direction class; it equals the pseudo-inverse matrices of Appendix A.
+template <class L, class R>
+__device__ __forceinline__ R fB_dir(int i, const R (&t)[L::C], R inv_tau_f) {
+  if (L::D == 2) {
+    const R a = t[0], s = t[1], b = t[2];
+    const int x = L::cx(i), y = L::cy(i);
+    R v;
+    if (i == 0) v = (a + b) * R(1.0 / 3.0);
+    else if (y == 0) v = (R(2) * b - a) * R(1.0 / 6.0);
+    else if (x == 0) v = (R(2) * a - b) * R(1.0 / 6.0);
+    else v = -(R(3 * x * y) * s + R(2) * (a + b)) * R(1.0 / 12.0);
+    return v * inv_tau_f;
+  } else {
+    const int c0 = L::cx(i), c1 = L::cy(i), c2 = L::cz(i);
+    const int n = c0 * c0 + c1 * c1 + c2 * c2;
+    R v;
+    if (n == 0) {
+      v = (t[0] + t[1] + t[2]) * R(5.0 / 21.0);
+    } else if (n == 1) {
+      const int a = c0 != 0 ? 0 : (c1 != 0 ? 1 : 2);
+      const R taa = t[a];
+      const R rest = t[0] + t[1] + t[2] - taa;
+      v = -taa * R(1.0 / 42.0) + rest * R(1.0 / 7.0);
+    } else {
+      const int g = c0 == 0 ? 0 : (c1 == 0 ? 1 : 2);  // axis normal to the plane
+      const int a = g == 0 ? 1 : 0, b = g == 2 ? 1 : 2;
+      const R sab = t[sym<L>(a, b)];
+      const int cab = cc<L>(i, a) * cc<L>(i, b);
+      v = -(t[a] + t[b]) * R(5.0 / 42.0) + t[g] * R(1.0 / 21.0) -
+          R(0.25) * R(cab) * sab;
+    }
+    return v * inv_tau_f;
+  }
+}
+
+// (grad u)_{ab} = d_a u_b, chi = -(A - I)/lambda + A.grad u + (grad u)^T.A
+// in compact components (Sec. 2.3); Ad = A - I.
+template <class L, class R>
+__device__ __forceinline__ void chi_tensor(const R (&A)[L::C], const R (&Ad)[L::C],
+                                           const R (&g)[L::D][L::D], R inv_lam,
+                                           R (&chi)[L::C]) {
+#pragma unroll
+  for (int k = 0; k < L::C; ++k) {
+    const int a = L::ca(k), b = L::cb(k);
+    R v = -Ad[k] * inv_lam;
+#pragma unroll
+    for (int q = 0; q < L::D; ++q) {
+      v += A[sym<L>(a, q)] * g[q][b] + g[q][a] * A[sym<L>(q, b)];
+    }
+    chi[k] = v;
+  }
+}
+
+}  // namespace fvlb

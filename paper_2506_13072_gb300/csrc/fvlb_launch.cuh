@@ -1,0 +1,170 @@
+// fvlb_launch.cuh -- host-side launch logic, templated on the lattice; each
+// lattice's translation unit instantiates it once.
+#pragma once
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "fvlb_internal.h"
+#include "fvlb_kernels.cuh"
+
+namespace fvlb {
+
+// Tile shapes of the fused step.  2D: a run of TX nodes along x marching
+// along y.  3D: TX x TY nodes in x-y marching along z (a warp spans x, so
+// every population load and store is one coalesced 128-byte line, shifted by
+// at most one element for the pushes).  HOLD_H keeps a site's stress
+// populations in registers between the conformation sum and the collision
+// (one read); MINB is the number of resident blocks per SM the register
+// allocation must allow.
+struct TileCfg {
+  int TX, TY, MINB;
+  bool HOLD_H;
+};
+
+// Launch-shape overrides from the environment, for tuning sweeps.
+inline int tune_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+template <class R>
+Phys<R> make_phys(const StepDesc& d) {
+  Phys<R> p;
+  p.tau_f = R(d.tau_f);
+  p.inv_tau_f = R(1.0 / d.tau_f);
+  p.inv_tau_h = R(1.0 / d.tau_h);
+  p.kh = R(1.0 - 0.5 / d.tau_h);
+  p.kf = R(1.0 - 0.5 / d.tau_f);
+  p.eta_over_lam = R(d.eta_p / d.lambda);
+  p.inv_lam = R(1.0 / d.lambda);
+  p.four_roll = d.four_roll;
+  p.Fv[0] = R(d.Fv[0]);
+  p.Fv[1] = R(d.Fv[1]);
+  p.Fv[2] = R(d.Fv[2]);
+  p.amp = R(d.amp);
+  const R* t = static_cast<const R*>(d.tables);
+  p.sx = t;
+  p.cxs = t ? t + d.nx : nullptr;
+  p.sy = t ? t + 2 * d.nx : nullptr;
+  p.cys = t ? t + 2 * d.nx + d.ny : nullptr;
+  p.first = d.first;
+  p.step = (uint32_t)d.step;
+  return p;
+}
+
+inline int grid_stride_blocks(long long N, int threads, int sms) {
+  const long long want = (N + threads - 1) / threads;
+  const long long cap = (long long)std::max(sms, 1) * 16;
+  return (int)std::max<long long>(1, std::min(want, cap));
+}
+
+template <class L, class S, int TX, int TY, bool HOLD_H, int MINB>
+cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
+                         const Bufs<S>& b) {
+  if (L::D == 2 && TY != 1) return cudaErrorInvalidValue;
+  const int bx = (d.nx + TX - 1) / TX;
+  const int by = L::D == 3 ? (d.ny + TY - 1) / TY : 1;
+  const int nm = L::D == 3 ? g.nz : d.ny;
+  // chunks along the march axis: enough blocks for several waves, but at
+  // least `min_chunk` planes so the two halo planes stay a small overhead
+  const int waves = tune_int("FVLB_WAVES", 8);
+  const int min_chunk = tune_int("FVLB_MIN_CHUNK", 8);
+  const long long target = (long long)std::max(d.sms, 1) * 2 * waves;
+  int nchunk = (int)std::max<long long>(1, target / std::max(1, bx * by));
+  int mchunk = std::max(min_chunk, (nm + nchunk - 1) / nchunk);
+  mchunk = std::min(mchunk, nm);
+  nchunk = (nm + mchunk - 1) / mchunk;
+  dim3 grid(bx, by, nchunk);
+  k_step_fused<L, S, TX, (L::D == 2 ? 1 : TY), HOLD_H, MINB>
+      <<<grid, TX * (L::D == 2 ? 1 : TY), 0, d.stream>>>(g, ph, b, mchunk);
+  return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t step_impl(const StepDesc& d) {
+  using R = RT<S>;
+  using X = typename Store<S>::X;
+  Grid g{d.nx, d.ny, L::D == 3 ? d.nz : 1, d.walls, d.pitch};
+  Phys<R> ph = make_phys<R>(d);
+  Bufs<S> b{static_cast<const S*>(d.f_in), static_cast<S*>(d.f_out),
+            static_cast<const S*>(d.h_in), static_cast<S*>(d.h_out),
+            static_cast<X*>(d.chi)};
+  if (d.variant == 0) {
+    const int cfg = tune_int("FVLB_TILE", 0);
+    if constexpr (L::D == 2) {
+      switch (cfg) {
+        case 1: return launch_fused<L, S, 128, 1, true, 4>(d, g, ph, b);
+        case 2: return launch_fused<L, S, 256, 1, true, 2>(d, g, ph, b);
+        case 3: return launch_fused<L, S, 64, 1, true, 8>(d, g, ph, b);
+        case 4: return launch_fused<L, S, 128, 1, false, 6>(d, g, ph, b);
+        default: return launch_fused<L, S, 128, 1, true, 1>(d, g, ph, b);
+      }
+    } else {
+      switch (cfg) {
+        case 1: return launch_fused<L, S, 32, 4, true, 2>(d, g, ph, b);
+        case 2: return launch_fused<L, S, 32, 2, true, 4>(d, g, ph, b);
+        case 3: return launch_fused<L, S, 32, 8, false, 2>(d, g, ph, b);
+        case 4: return launch_fused<L, S, 32, 4, true, 1>(d, g, ph, b);
+        default: return launch_fused<L, S, 32, 8, true, 1>(d, g, ph, b);
+      }
+    }
+  } else {
+    const int threads = 128;
+    const int blocks = grid_stride_blocks(d.N, threads, d.sms);
+    R* ubuf = static_cast<R*>(d.ubuf);
+    k_velocity<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, d.N);
+    k_collide_split<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, d.N);
+  }
+  return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t init_impl(const InitDesc& d) {
+  Grid g{d.nx, d.ny, L::D == 3 ? d.nz : 1, 0, d.pitch};
+  const int threads = 256;
+  const int blocks = grid_stride_blocks(d.N, threads, d.sms);
+  k_init<L, S><<<blocks, threads, 0, d.stream>>>(
+      g, static_cast<S*>(d.f), static_cast<S*>(d.h),
+      static_cast<typename Store<S>::X*>(d.chi), d.u0, d.p0, d.A0, d.N);
+  return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t fields_impl(const StepDesc& d, int which, double* out) {
+  using R = RT<S>;
+  Grid g{d.nx, d.ny, L::D == 3 ? d.nz : 1, d.walls, d.pitch};
+  Phys<R> ph = make_phys<R>(d);
+  const int threads = 256;
+  const int blocks = grid_stride_blocks(d.N, threads, d.sms);
+  k_fields<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, static_cast<const S*>(d.f_in),
+                                                   static_cast<const S*>(d.h_in), which, out,
+                                                   d.N);
+  return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t reduce_impl(const StepDesc& d, double* part, double* out) {
+  using R = RT<S>;
+  Grid g{d.nx, d.ny, L::D == 3 ? d.nz : 1, d.walls, d.pitch};
+  Phys<R> ph = make_phys<R>(d);
+  const int nparts = reduce_parts(d.N);
+  k_reduce_partial<L, S><<<nparts, kReduceThreads, 0, d.stream>>>(
+      g, ph, static_cast<const S*>(d.f_in), static_cast<const S*>(d.h_in), part, d.N);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return reduce_finalize(part, nparts, d.N, out, d.stream);
+}
+
+#define FVLB_DISPATCH(storage, CALL)                              \
+  switch (storage) {                                              \
+    case kFP64: return CALL(double);                              \
+    case kFP32: return CALL(float);                               \
+    case kFP16Dev: return CALL(__half);                           \
+    case kBF16Dev: return CALL(__nv_bfloat16);                    \
+    case kFP16DevSR: return CALL(half_sr);                        \
+    case kBF16DevSR: return CALL(bf16_sr);                        \
+    default: return cudaErrorInvalidValue;                        \
+  }
+
+}  // namespace fvlb

@@ -1,0 +1,32 @@
+// k_d2q9.cu -- D2Q9 instantiation of the step, initialisation, field and
+// diagnostics launchers (one translation unit per lattice so that the two
+// lattices compile in parallel).
+#include "fvlb_launch.cuh"
+
+namespace fvlb {
+
+cudaError_t step_d2q9(const StepDesc& d) {
+#define CALL(S) step_impl<D2Q9, S>(d)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
+cudaError_t init_d2q9(const InitDesc& d) {
+#define CALL(S) init_impl<D2Q9, S>(d)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
+cudaError_t fields_d2q9(const StepDesc& d, int which, double* out) {
+#define CALL(S) fields_impl<D2Q9, S>(d, which, out)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
+cudaError_t reduce_d2q9(const StepDesc& d, double* part, double* out) {
+#define CALL(S) reduce_impl<D2Q9, S>(d, part, out)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
+}  // namespace fvlb

@@ -1,0 +1,339 @@
+"""Python binding of the fvlb C ABI (include/fvlb.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libfvlb.so``.  There is no CPU fallback; if the library is missing
+the import of this module fails.  PyTorch supplies device memory (through the
+library's allocator hooks, backed by torch's caching allocator) and the CUDA
+stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfvlb.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "fvlb.h")
+
+FVLB_D2Q9 = 9
+FVLB_D3Q19 = 19
+
+FVLB_OK = 0
+FVLB_EINVAL = -1
+FVLB_ENOMEM = -2
+FVLB_ECUDA = -3
+FVLB_EUNSTABLE = -4
+FVLB_ETIMEOUT = -5
+FVLB_ESTATE = -6
+
+FVLB_FORCE_NONE = 0
+FVLB_FORCE_CONST = 1
+FVLB_FORCE_FOUR_ROLL = 2
+FVLB_FORCE_COSINE = 3
+
+FVLB_FP64 = 0
+FVLB_FP32 = 1
+FVLB_FP16_DEV = 2
+FVLB_BF16_DEV = 3
+FVLB_FP16_DEV_SR = 4
+FVLB_BF16_DEV_SR = 5
+
+FVLB_KERNEL_FUSED = 0
+FVLB_KERNEL_SPLIT = 1
+
+FVLB_FIELD_U = 0
+FVLB_FIELD_P = 1
+FVLB_FIELD_A = 2
+FVLB_FIELD_TAU_P = 3
+
+PRECISIONS = {"fp64": FVLB_FP64, "fp32": FVLB_FP32, "fp16_dev": FVLB_FP16_DEV,
+              "bf16_dev": FVLB_BF16_DEV, "fp16_dev_sr": FVLB_FP16_DEV_SR,
+              "bf16_dev_sr": FVLB_BF16_DEV_SR}
+
+
+class FvlbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fvlb error {code}: {msg}")
+        self.code = code
+
+
+class fvlb_force(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("F0", ctypes.c_double * 3),
+                ("k", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"the CUDA library {LIB_PATH} is not built; run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+_H = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "fvlb_set_allocator": ([ALLOC_FN, FREE_FN, ctypes.c_void_p], ctypes.c_int),
+    "fvlb_create": ([ctypes.POINTER(_H), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                     ctypes.POINTER(fvlb_force)], ctypes.c_int),
+    "fvlb_set_walls": ([_H, ctypes.c_uint], ctypes.c_int),
+    "fvlb_set_precision": ([_H, ctypes.c_int], ctypes.c_int),
+    "fvlb_set_kernel": ([_H, ctypes.c_int], ctypes.c_int),
+    "fvlb_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
+    "fvlb_init_fields": ([_H, _dp, _dp, _dp], ctypes.c_int),
+    "fvlb_step": ([_H, ctypes.c_long], ctypes.c_int),
+    "fvlb_fields": ([_H, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+    "fvlb_reduce": ([_H, _dp], ctypes.c_int),
+    "fvlb_synchronize": ([_H], ctypes.c_int),
+    "fvlb_get_time": ([_H, ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
+    "fvlb_state_size": ([_H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "fvlb_save_state": ([_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "fvlb_load_state": ([_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "fvlb_bytes_per_update": ([_H, _dp], ctypes.c_int),
+    "fvlb_last_error": ([_H], ctypes.c_char_p),
+    "fvlb_destroy": ([_H], ctypes.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+def header_symbols(path: str = HEADER_PATH):
+    """Names of the entry points declared in include/fvlb.h."""
+    with open(path) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fvlb_[a-z0-9_]+)\s*\(", text)))
+
+
+def last_error(h=None) -> str:
+    msg = lib.fvlb_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def check(code, h=None):
+    if code != FVLB_OK:
+        raise FvlbError(code, last_error(h))
+    return code
+
+
+# ---------------------------------------------------------------------------
+# Device memory from torch's caching allocator
+# ---------------------------------------------------------------------------
+_alloc_refs = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching
+    allocator (on the current device and stream)."""
+    global _alloc_refs
+    import torch
+
+    if _alloc_refs is not None:
+        return
+
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
+        except Exception:  # out of memory -> the library reports FVLB_ENOMEM
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    check(lib.fvlb_set_allocator(a, f, None))
+    _alloc_refs = (a, f)
+
+
+def use_cuda_allocator():
+    global _alloc_refs
+    check(lib.fvlb_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _alloc_refs = None
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+class Simulation:
+    """One fvlb handle.
+
+    ``lattice`` is FVLB_D2Q9 or FVLB_D3Q19; field arrays use the grid shape
+    (ny, nx) or (nz, ny, nx) with components last: u [..., D], p [...],
+    A and tau_p [..., C] in compact symmetric order (2D xx, xy, yy; 3D xx,
+    yy, zz, xy, xz, yz).
+    """
+
+    def __init__(self, lattice, nx, ny, nz=1, tau_s=0.8, eta_p=0.0, lam=1.0,
+                 force_kind=FVLB_FORCE_NONE, F0=(0.0, 0.0, 0.0), k=0.0, omega=0.0,
+                 walls=0, precision=FVLB_FP64, kernel=FVLB_KERNEL_FUSED, stream=None):
+        self.lattice = lattice
+        self.D = 2 if lattice == FVLB_D2Q9 else 3
+        self.C = 3 if self.D == 2 else 6
+        self.nx, self.ny, self.nz = nx, ny, (1 if self.D == 2 else nz)
+        self.N = self.nx * self.ny * self.nz
+        frc = fvlb_force()
+        frc.kind = int(force_kind)
+        for a in range(3):
+            frc.F0[a] = float(F0[a]) if a < len(F0) else 0.0
+        frc.k, frc.omega = float(k), float(omega)
+        h = _H()
+        check(lib.fvlb_create(ctypes.byref(h), int(lattice), int(nx), int(ny), int(self.nz),
+                              float(tau_s), float(eta_p), float(lam), ctypes.byref(frc)))
+        self.h = h
+        try:
+            check(lib.fvlb_set_walls(h, int(walls)), h)
+            if isinstance(precision, str):
+                precision = PRECISIONS[precision]
+            check(lib.fvlb_set_precision(h, int(precision)), h)
+            check(lib.fvlb_set_kernel(h, int(kernel)), h)
+            if stream is not None:
+                self.set_stream(stream)
+        except Exception:
+            lib.fvlb_destroy(h)
+            self.h = None
+            raise
+
+    @classmethod
+    def from_problem(cls, pr, **kw):
+        s = cls(pr.lattice, pr.nx, pr.ny, pr.nz, pr.tau_s, pr.eta_p, pr.lam, pr.force_kind,
+                pr.F0, pr.k, pr.omega, pr.walls, **kw)
+        return s
+
+    # -- life cycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fvlb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration -------------------------------------------------------
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        check(lib.fvlb_set_stream(self.h, ctypes.c_void_p(ptr or 0)), self.h)
+
+    def set_kernel(self, variant):
+        check(lib.fvlb_set_kernel(self.h, int(variant)), self.h)
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx) if self.D == 2 else (self.nz, self.ny, self.nx)
+
+    # -- state ---------------------------------------------------------------
+    def init_fields(self, u=None, p=None, A=None):
+        """u [..., D], p [...], A [..., C] (compact) or [..., D, D] (full)."""
+        N, D, C = self.N, self.D, self.C
+        uu = None if u is None else np.ascontiguousarray(np.asarray(u, np.float64).reshape(N * D))
+        pp = None if p is None else np.ascontiguousarray(np.asarray(p, np.float64).reshape(N))
+        AA = None
+        if A is not None:
+            A = np.asarray(A, np.float64)
+            if A.shape[-2:] == (D, D):
+                A = full_to_compact(A)
+            AA = np.ascontiguousarray(A.reshape(N * C))
+        check(lib.fvlb_init_fields(self.h, _ptr(uu), _ptr(pp), _ptr(AA)), self.h)
+
+    def step(self, n=1):
+        check(lib.fvlb_step(self.h, int(n)), self.h)
+
+    def synchronize(self):
+        check(lib.fvlb_synchronize(self.h), self.h)
+
+    @property
+    def t(self):
+        t = ctypes.c_long()
+        check(lib.fvlb_get_time(self.h, ctypes.byref(t)), self.h)
+        return t.value
+
+    def fields(self, which, out=None):
+        nc = {FVLB_FIELD_U: self.D, FVLB_FIELD_P: 1, FVLB_FIELD_A: self.C,
+              FVLB_FIELD_TAU_P: self.C}[which]
+        if out is None:
+            out = np.empty(self.N * nc, np.float64)
+        check(lib.fvlb_fields(self.h, int(which), _ptr(out), out.size), self.h)
+        shp = self.shape if nc == 1 else self.shape + (nc,)
+        return out.reshape(shp)
+
+    def u(self):
+        return self.fields(FVLB_FIELD_U)
+
+    def p(self):
+        return self.fields(FVLB_FIELD_P)
+
+    def A(self):
+        return self.fields(FVLB_FIELD_A)
+
+    def tau_p(self):
+        return self.fields(FVLB_FIELD_TAU_P)
+
+    def reduce(self, check_finite=True):
+        out = np.zeros(8)
+        r = lib.fvlb_reduce(self.h, _ptr(out))
+        if r != FVLB_OK and not (r == FVLB_EUNSTABLE and not check_finite):
+            raise FvlbError(r, last_error(self.h))
+        return dict(mass=out[0], momentum=out[1:4].copy(), KE=out[4], PE=out[5],
+                    nonfinite=int(out[6]), umax=out[7])
+
+    def state_size(self):
+        n = ctypes.c_size_t()
+        check(lib.fvlb_state_size(self.h, ctypes.byref(n)), self.h)
+        return n.value
+
+    def save_state(self):
+        buf = np.empty(self.state_size(), np.uint8)
+        check(lib.fvlb_save_state(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.size), self.h)
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        check(lib.fvlb_load_state(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.size), self.h)
+
+    def bytes_per_update(self):
+        b = ctypes.c_double()
+        check(lib.fvlb_bytes_per_update(self.h, ctypes.byref(b)), self.h)
+        return b.value
+
+
+def full_to_compact(A):
+    """[..., D, D] -> [..., C] in the library's compact order."""
+    D = A.shape[-1]
+    if D == 2:
+        return np.stack([A[..., 0, 0], A[..., 0, 1], A[..., 1, 1]], -1)
+    return np.stack([A[..., 0, 0], A[..., 1, 1], A[..., 2, 2], A[..., 0, 1], A[..., 0, 2],
+                     A[..., 1, 2]], -1)
+
+
+def compact_to_full(A):
+    C = A.shape[-1]
+    if C == 3:
+        out = np.empty(A.shape[:-1] + (2, 2))
+        out[..., 0, 0], out[..., 0, 1], out[..., 1, 0], out[..., 1, 1] = \
+            A[..., 0], A[..., 1], A[..., 1], A[..., 2]
+        return out
+    out = np.empty(A.shape[:-1] + (3, 3))
+    idx = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (0, 1): 3, (0, 2): 4, (1, 2): 5}
+    for (a, b), k in idx.items():
+        out[..., a, b] = A[..., k]
+        out[..., b, a] = A[..., k]
+    return out

@@ -1,0 +1,101 @@
+"""Helpers shared by the GPU tests: run the CUDA library and the FP64 oracle
+on the same seeded problem and compare them."""
+import numpy as np
+
+import oracle as O
+from paper_2506_13072_gb300 import workloads as W
+
+_fvlb = None
+
+
+def fvlb():
+    """The binding, with device memory routed through torch's allocator."""
+    global _fvlb
+    if _fvlb is None:
+        import torch
+
+        torch.cuda.init()
+        from paper_2506_13072_gb300 import fvlb as F
+
+        F.use_torch_allocator()
+        _fvlb = F
+    return _fvlb
+
+
+def rel_l2(x, ref, floor):
+    """||x - ref||_2 / ||ref||_2, or / floor when ||ref|| is below it."""
+    d = np.linalg.norm(np.ravel(x) - np.ravel(ref))
+    n = np.linalg.norm(np.ravel(ref))
+    return d / max(n, floor)
+
+
+def compact(A):
+    return fvlb().full_to_compact(A)
+
+
+def gpu_sim(pr, precision, kernel=0):
+    F = fvlb()
+    s = F.Simulation.from_problem(pr, precision=precision, kernel=kernel)
+    s.init_fields(pr.u0, pr.p0, pr.A0)
+    return s
+
+
+def oracle_sim(pr):
+    o = O.Oracle(pr.lattice, **pr.oracle_kwargs())
+    o.init(u=pr.u0, p=pr.p0, A=pr.A0)
+    return o
+
+
+def compare(pr, steps, precision, tol, kernel=0, chunks=1, fields=("u", "p", "tau_p", "A")):
+    """Advance both sides `steps` steps (in `chunks` pieces) and return the
+    worst relative L2 error per field; assert each is <= tol."""
+    s = gpu_sim(pr, precision, kernel)
+    o = oracle_sim(pr)
+    worst = {k: 0.0 for k in fields}
+    per = steps // chunks
+    for c in range(chunks):
+        n = per if c < chunks - 1 else steps - per * (chunks - 1)
+        s.step(n)
+        o.step(n)
+        got = dict(u=s.u(), p=s.p(), tau_p=s.tau_p(), A=s.A())
+        ref = dict(u=o.u(), p=o.p(), tau_p=compact(o.tau_p()), A=compact(o.A()))
+        # p is recovered from sum_{i!=0} f_i, populations of size |u|, while
+        # p itself is of size |u|^2: its error is measured against the
+        # dynamic-pressure scale ||u||_2 max|u| when that is larger than ||p||.
+        # Conditioning-aware norms (each side's own rounding sets a floor that
+        # a plain relative norm would amplify):
+        #  - p is recovered as c_s^2/(1 - w_0) sum_{i!=0} f_i + ..., a sum of
+        #    populations of size |u|, so its error is measured against
+        #    max(||p||, 0.1 ||u||);
+        #  - tau_p = (eta_p/lambda)(A - I) is formed by the oracle from its
+        #    full-tensor A (stored as h ~ w_i A), whose rounding is relative to
+        #    ||A||, so its error is measured against
+        #    max(||tau_p||, 1e-2 (eta_p/lambda) ||A||).
+        un = np.linalg.norm(ref["u"])
+        tfloor = 1e-2 * pr.eta_p / pr.lam * np.linalg.norm(ref["A"]) + 1e-30
+        floors = dict(u=1e-30, p=0.1 * un + 1e-30, tau_p=tfloor, A=1.0)
+        for k in fields:
+            worst[k] = max(worst[k], rel_l2(got[k], ref[k], floors[k]))
+    s.close()
+    bad = {k: v for k, v in worst.items() if not v <= tol}
+    assert not bad, f"rel-L2 above {tol}: {worst}"
+    return worst
+
+
+def tiled_problem(pr_small, reps):
+    """The same problem on a grid `reps` times larger per axis, with the
+    initial fields tiled; a periodic problem whose fields have the small
+    grid's period evolves as the small one tiled."""
+    import copy
+
+    pr = copy.deepcopy(pr_small)
+    D = pr.D
+    pr.nx *= reps
+    pr.ny *= reps
+    if D == 3:
+        pr.nz *= reps
+    tile = (reps,) * D
+    pr.u0 = np.tile(pr_small.u0, tile + (1,))
+    pr.p0 = np.tile(pr_small.p0, tile)
+    pr.A0 = np.tile(pr_small.A0, tile + (1, 1))
+    return pr
