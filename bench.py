@@ -322,7 +322,7 @@ def run_ours(args, rank, world, dist):
                      "traffic": tr["dram_bytes_per_launch"] if tr else None,
                      "algorithmic_bytes_per_launch": bpu * sites,
                      "bytes_per_update": bpu, "peak_source": f"{which} hbm_gbs (copy)",
-                     "kernel": "k_step_fused<D3Q19,float,32,8>"},
+                     "kernel": "k_step_fused<D3Q19,float,GX=1,TY=2> (32x2 nodes x 6 components)"},
         "e2e": {"value": round(sites * e2e_steps / e2e_dt / 1e6, 1), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "fvlb_init_fields from host + K steps + fvlb_fields(U) to host"},

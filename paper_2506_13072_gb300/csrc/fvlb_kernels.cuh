@@ -227,105 +227,175 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
 }
 
 // ---------------------------------------------------------------------------
-// Fused step: one launch per time step.
+// Fused step: one launch per time step, component-parallel.
 //
-// A block owns a TX x TY tile of the plane orthogonal to the march axis
-// (2D: a run of TX nodes along x, TY = 1, marching along y; 3D: TX x TY in
-// x-y, marching along z) and a chunk of `mchunk` planes along the march
-// axis.  For each plane it first computes the velocity of the tile plus a
-// one-node halo into a three-plane shared-memory ring, then collides the
-// tile using central differences from the ring.  Velocities on halo nodes
-// are recomputed from their populations (read through L2) rather than
-// exchanged, so no block waits on another.
+// Tile: a block owns GX x TY groups of 32 consecutive x-nodes (2D: GX groups
+// in one row, TY = 1; 3D: GX x TY groups in an x-y tile) and marches along
+// the slowest axis (2D: y, 3D: z) over a chunk of `mchunk` planes.
+//
+// Work split: each node of a plane is updated by C threads, one per
+// symmetric stress component k (C = 3 in 2D, 6 in 3D), in C different warps
+// of the same group, so a warp reads and writes one component's populations
+// h_{k,i} of 32 consecutive nodes (coalesced).  Thread k also collides and
+// pushes the flow populations f_i with i = k (mod C).  The nodes' A - I
+// components and the partial sums of f entering the pressure are exchanged
+// through shared memory.  Holding Q + ceil(Q/C) populations instead of
+// Q (1 + C) keeps the register footprint low enough for many resident warps.
+//
+// Velocity gradient: the same-step velocity of the tile and a one-node halo
+// is kept in a three-plane shared-memory ring (planes m-1, m, m+1), filled
+// from the populations of each plane one iteration ahead; halo velocities
+// are recomputed from their populations (read through L2), so blocks never
+// wait on each other.  Per plane: one memory phase (the ring fill of plane
+// m+1 and the collision loads of plane m are issued together), two barriers.
 // ---------------------------------------------------------------------------
-template <class L, class S, int TX, int TY, bool HOLD_H, int MINB>
-__global__ void __launch_bounds__(TX* TY, MINB)
+template <class L>
+struct Split {
+  // number of flow directions owned by component k
+  __host__ __device__ static constexpr int nf(int k) { return (L::Q - k + L::C - 1) / L::C; }
+  static constexpr int NFMAX = (L::Q + L::C - 1) / L::C;
+};
+
+template <class L, class S, int GX, int TY, int MINB>
+__global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
     k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
   using R = RT<S>;
-  constexpr int D = L::D, Q = L::Q;
-  constexpr int NT = TX * TY;
-  constexpr int EX = TX + 2;
+  using X = typename Store<S>::X;
+  constexpr int D = L::D, Q = L::Q, C = L::C;
+  constexpr int NG = GX * TY;           // groups of 32 nodes per plane tile
+  constexpr int NT = NG * C * 32;       // threads
+  constexpr int TXS = GX * 32;          // tile extent along x
+  constexpr int EX = TXS + 2;
   constexpr int EY = (D == 3) ? TY + 2 : 1;
-  constexpr int NE = EX * EY;
+  constexpr int NE = EX * EY;           // ring slots per plane
+  constexpr int NS = NG * 32;           // nodes per plane tile
+  constexpr int NFM = Split<L>::NFMAX;
   static_assert(D == 3 || TY == 1, "2D tiles are one row high");
+  static_assert(NE <= NT, "one ring slot per thread at most");
   __shared__ R ring[3][D][NE];
+  __shared__ R sAd[C][NS];              // A - I of the tile nodes
+  __shared__ R sPf[C][NS];              // partial sums of f_{i != 0}
 
   const int nx = g.nx, ny = g.ny;
   const int nm = (D == 3) ? g.nz : g.ny;
   const bool wall_x = g.walls & 1;
   const bool wall_y = (D == 3) && ((g.walls >> 1) & 1);
   const bool wall_m = (g.walls >> (D - 1)) & 1;
-  const int x0 = blockIdx.x * TX;
+  const int x0 = blockIdx.x * TXS;
   const int y0 = (D == 3) ? blockIdx.y * TY : 0;
   const int m0 = blockIdx.z * mchunk;
   const int m1 = min(m0 + mchunk, nm);
+  const long long P = g.pitch;
+
   const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int grp = warp / C;
+  const int k = warp - grp * C;         // stress component of this thread
+  const int gxi = grp % GX, gyi = grp / GX;
+  const int tx = gxi * 32 + lane;       // node of the tile
+  const int ty = gyi;
+  const int node = grp * 32 + lane;     // index into sAd / sPf
   const int x = x0 + tx;
   const int y = (D == 3) ? y0 + ty : 0;
   const bool active = (x < nx) && (D == 2 || y < ny);
   const int e_own = (D == 3) ? (ty + 1) * EX + tx + 1 : tx + 1;
-  const long long P = g.pitch;
 
-  // Velocity of every extended-tile slot of plane m into ring slot r.  A
-  // thread owns at most NR slots; all their population loads are issued
-  // before any velocity is formed, so the halo slots cost no second
-  // round-trip to memory.
-  constexpr int NR = (NE + NT - 1) / NT;
-  auto fill = [&](int m, int r) {
-    if (m < 0 || m >= nm) {
-      if (wall_m) return;
-      m = (m + nm) % nm;
+  // ring slot of this thread (if tid < NE)
+  int fgx = 0, fgy = 0;
+  bool fok = tid < NE;
+  if (fok) {
+    const int ex = tid % EX, ey = tid / EX;
+    fgx = x0 + ex - 1;
+    fgy = (D == 3) ? y0 + ey - 1 : 0;
+    if (fgx < 0 || fgx >= nx) {
+      if (wall_x) fok = false;
+      else fgx = ((fgx % nx) + nx) % nx;
     }
-    R fv[NR][Q];
-    bool ok[NR];
-    int gxs[NR], gys[NR];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      const int e = tid + q * NT;
-      ok[q] = e < NE;
-      const int ex = e % EX, ey = e / EX;
-      int gx = x0 + ex - 1;
-      int gy = (D == 3) ? y0 + ey - 1 : 0;
-      if (gx < 0 || gx >= nx) {
-        if (wall_x) ok[q] = false;
-        else gx = ((gx % nx) + nx) % nx;
-      }
-      if (D == 3 && (gy < 0 || gy >= ny)) {
-        if (wall_y) ok[q] = false;
-        else gy = ((gy % ny) + ny) % ny;
-      }
-      gxs[q] = gx;
-      gys[q] = gy;
-      if (ok[q]) {
-        const long long s = (D == 3) ? ((long long)m * ny + gy) * nx + gx
-                                     : (long long)m * nx + gx;
-        load_f<L, S>(b.f_in, P, s, fv[q]);
-      }
+    if (D == 3 && (fgy < 0 || fgy >= ny)) {
+      if (wall_y) fok = false;
+      else fgy = ((fgy % ny) + ny) % ny;
     }
+  }
+  auto plane_of = [&](int m) -> int {  // -1: beyond a wall
+    if (m < 0 || m >= nm) return wall_m ? -1 : (m + nm) % nm;
+    return m;
+  };
+  auto slot_site = [&](int m) -> long long {
+    return (D == 3) ? ((long long)m * ny + fgy) * nx + fgx : (long long)m * nx + fgx;
+  };
+  auto fill_u = [&](const R (&fv)[Q], int m, int r) {
+    R u[D];
 #pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      const int e = tid + q * NT;
-      if (e >= NE) continue;
-      R u[D];
+    for (int a = 0; a < D; ++a) u[a] = R(0);
+    R F[3];
+    body_force<L, R>(ph, fgx, D == 3 ? fgy : m, F);
+    velocity<L, R>(fv, F, u);
 #pragma unroll
-      for (int a = 0; a < D; ++a) u[a] = R(0);
-      if (ok[q]) {
-        R F[3];
-        body_force<L, R>(ph, gxs[q], D == 3 ? gys[q] : m, F);
-        velocity<L, R>(fv[q], F, u);
-      }
+    for (int a = 0; a < D; ++a) ring[r][a][tid] = u[a];
+  };
+  auto fill_zero = [&](int r) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) ring[r][a][e] = u[a];
-    }
+    for (int a = 0; a < D; ++a) ring[r][a][tid] = R(0);
   };
 
-  fill(m0 - 1, 0);
-  fill(m0, 1);
+  // prologue: planes m0 - 1 and m0
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int mm = plane_of(m0 - 1 + q);
+    if (tid < NE) {
+      if (fok && mm >= 0) {
+        R fv[Q];
+        load_f<L, S>(b.f_in, P, slot_site(mm), fv);
+        fill_u(fv, mm, q);
+      } else {
+        fill_zero(q);
+      }
+    }
+  }
+  __syncthreads();
+
   for (int m = m0; m < m1; ++m) {
     const int rm = (m - m0) % 3, rc = (m - m0 + 1) % 3, rp = (m - m0 + 2) % 3;
-    fill(m + 1, rp);
+    const long long s = (D == 3) ? ((long long)m * ny + y) * nx + x : (long long)m * nx + x;
+
+    // ---- memory phase: ring fill of plane m + 1 and this node's populations
+    const int mn = plane_of(m + 1);
+    const bool do_fill = tid < NE && fok && mn >= 0;
+    R fn[Q];
+    if (do_fill) load_f<L, S>(b.f_in, P, slot_site(mn), fn);
+    R hv[Q], fo[NFM];
+    R old = R(0);
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) hv[i] = load_h<L, S>(b.h_in, P, s, k, i);
+#pragma unroll
+      for (int j = 0; j < NFM; ++j) {
+        const int i = k + j * C;
+        fo[j] = i < Q ? Store<S>::ld(b.f_in + i * P + s) : R(0);
+      }
+      old = R(b.chi[k * P + s]);
+    }
+    if (tid < NE) {
+      if (do_fill) fill_u(fn, mn, rp);
+      else fill_zero(rp);
+    }
+    if (active) {
+      R a = R(0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a += hv[i];
+      sAd[k][node] = a;
+      R pf = R(0);
+#pragma unroll
+      for (int j = 0; j < NFM; ++j) {
+        const int i = k + j * C;
+        if (i != 0 && i < Q) pf += fo[j];
+      }
+      sPf[k][node] = pf;
+    }
     __syncthreads();
+
+    // ---- collision phase ----------------------------------------------------
     if (active) {
       R u[D], gr[D][D];
 #pragma unroll
@@ -333,7 +403,6 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 #pragma unroll
       for (int bq = 0; bq < D; ++bq) {
         const R uo = u[bq];
-        // x
         {
           const R up = ring[rc][bq][e_own + 1], um = ring[rc][bq][e_own - 1];
           R d = R(0.5) * (up - um);
@@ -356,13 +425,131 @@ __global__ void __launch_bounds__(TX* TY, MINB)
           gr[D - 1][bq] = d;
         }
       }
-      const long long s = (D == 3) ? ((long long)m * ny + y) * nx + x : (long long)m * nx + x;
-      R fv[Q];
-      load_f<L, S>(b.f_in, P, s, fv);
+      R Ad[C];
+#pragma unroll
+      for (int q = 0; q < C; ++q) Ad[q] = sAd[q][node];
+      R sumf = R(0);
+#pragma unroll
+      for (int q = 0; q < C; ++q) sumf += sPf[q][node];
       R F[3];
       body_force<L, R>(ph, x, D == 3 ? y : m, F);
-      if (D == 3) collide_site<L, S, HOLD_H>(g, ph, b, s, x, y, m, u, gr, fv, F);
-      else collide_site<L, S, HOLD_H>(g, ph, b, s, x, m, 0, u, gr, fv, F);
+      R uu = R(0), Fu = R(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        uu += u[a] * u[a];
+        Fu += F[a] * u[a];
+      }
+      const R kB = ph.eta_over_lam * ph.inv_tau_f;
+      // pressure (Sec. 2.2, Appendix B)
+      constexpr double w0 = L::w(0);
+      const R fB0 = fB_dir<L, R>(0, Ad, kB);
+      const R p = R(1.0 / (3.0 * (1.0 - w0))) *
+                  (sumf + R(-1.5 * w0) * uu + ph.tau_f * (R(-3.0 * w0) * ph.kf * Fu) +
+                   ph.tau_f * fB0);
+
+      // stress source of this component (Sec. 2.3)
+      R Akk[C];
+#pragma unroll
+      for (int q = 0; q < C; ++q) Akk[q] = Ad[q] + (diag<L>(q) ? R(1) : R(0));
+      R chi_k = R(0), Ad_k = R(0), A_k = R(0);
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        if (q != k) continue;
+        const int a = L::ca(q), bb = L::cb(q);
+        R v = -Ad[q] * ph.inv_lam;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+          v += Akk[sym<L>(a, r)] * gr[r][bb] + gr[r][a] * Akk[sym<L>(r, bb)];
+        chi_k = v;
+        Ad_k = Ad[q];
+        A_k = Akk[q];
+      }
+      if (ph.first) old = chi_k;
+      b.chi[k * P + s] = X(chi_k);
+      const R src = R(1.5) * chi_k - R(0.5) * old;
+      uint32_t rng = Store<S>::sr
+                         ? hash32(((uint32_t)s * 8u + (uint32_t)k) * 0x9e3779b9u ^ hash32(ph.step))
+                         : 0u;
+
+      // per-site neighbour offsets along each axis (periodic wrap)
+      const long long strd[3] = {1, nx, (long long)nx * ny};
+      const int cz_ = (D == 3) ? m : 0;
+      const int pos[3] = {x, D == 3 ? y : m, cz_};
+      const int ext[3] = {nx, ny, g.nz};
+      long long offp[3], offm[3];
+      bool edgep[3], edgem[3];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        edgep[a] = pos[a] == ext[a] - 1;
+        edgem[a] = pos[a] == 0;
+        offp[a] = edgep[a] ? -(long long)(ext[a] - 1) * strd[a] : strd[a];
+        offm[a] = edgem[a] ? (long long)(ext[a] - 1) * strd[a] : -strd[a];
+      }
+      // destination of direction i: neighbour, or own node through a wall
+      auto dest = [&](int i, int& j) -> long long {
+        long long d = s;
+        bool bb = false;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int c = cc<L>(i, a);
+          if (c == 1) {
+            d += offp[a];
+            bb |= ((g.walls >> a) & 1) && edgep[a];
+          } else if (c == -1) {
+            d += offm[a];
+            bb |= ((g.walls >> a) & 1) && edgem[a];
+          }
+        }
+        j = bb ? L::opp(i) : i;
+        return bb ? s : d;
+      };
+
+      // h_k: h* = (1 - 1/tau_h) h + w_i [alpha + c_i.u beta] with
+      // alpha = (A-I)_k / tau_h + src and beta = 3 (A_k / tau_h + kh src)
+      const R om = ph.inv_tau_h;
+      const R alpha = om * Ad_k + src;
+      const R beta = R(3) * (om * A_k + ph.kh * src);
+      const R keep = R(1) - om;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        R cu = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int c = cc<L>(i, a);
+          if (c == 1) cu += u[a];
+          if (c == -1) cu -= u[a];
+        }
+        const R post = keep * hv[i] + R(L::w(i)) * (alpha + cu * beta);
+        int j;
+        const long long d = dest(i, j);
+        store_h<L, S>(b.h_out, P, d, k, j, post, Store<S>::sr ? lcg_next(rng) : 0u);
+      }
+
+      // f_i, i = k (mod C): f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
+#pragma unroll
+      for (int jj = 0; jj < NFM; ++jj) {
+#pragma unroll
+        for (int kk = 0; kk < C; ++kk) {
+          const int i = kk + jj * C;
+          if (kk != k || i >= Q) continue;
+          R cu = R(0), cF = R(0);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const int c = cc<L>(i, a);
+            if (c == 1) { cu += u[a]; cF += F[a]; }
+            if (c == -1) { cu -= u[a]; cF -= F[a]; }
+          }
+          const R wi = R(L::w(i));
+          const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
+          const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+          const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
+          const R fBi = fB_dir<L, R>(i, Ad, kB);
+          const R post = fo[jj] - (fo[jj] - feq) * ph.inv_tau_f + fBi + Fi;
+          int j;
+          const long long d = dest(i, j);
+          Store<S>::st(b.f_out + j * P + d, post, Store<S>::sr ? lcg_next(rng) : 0u);
+        }
+      }
     }
     __syncthreads();
   }

@@ -10,18 +10,11 @@
 
 namespace fvlb {
 
-// Tile shapes of the fused step.  2D: a run of TX nodes along x marching
-// along y.  3D: TX x TY nodes in x-y marching along z (a warp spans x, so
-// every population load and store is one coalesced 128-byte line, shifted by
-// at most one element for the pushes).  HOLD_H keeps a site's stress
-// populations in registers between the conformation sum and the collision
-// (one read); MINB is the number of resident blocks per SM the register
+// Tile shapes of the fused step: GX x TY groups of 32 x-consecutive nodes
+// (a warp spans x, so every population load and store is one coalesced
+// 128-byte line, shifted by at most one element for the pushes), C threads
+// per node; MINB is the number of resident blocks per SM the register
 // allocation must allow.
-struct TileCfg {
-  int TX, TY, MINB;
-  bool HOLD_H;
-};
-
 // Launch-shape overrides from the environment, for tuning sweeps.
 inline int tune_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
@@ -59,25 +52,24 @@ inline int grid_stride_blocks(long long N, int threads, int sms) {
   return (int)std::max<long long>(1, std::min(want, cap));
 }
 
-template <class L, class S, int TX, int TY, bool HOLD_H, int MINB>
+template <class L, class S, int GX, int TY, int MINB>
 cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                          const Bufs<S>& b) {
-  if (L::D == 2 && TY != 1) return cudaErrorInvalidValue;
-  const int bx = (d.nx + TX - 1) / TX;
+  constexpr int TXS = GX * 32;
+  const int bx = (d.nx + TXS - 1) / TXS;
   const int by = L::D == 3 ? (d.ny + TY - 1) / TY : 1;
   const int nm = L::D == 3 ? g.nz : d.ny;
   // chunks along the march axis: enough blocks for several waves, but at
   // least `min_chunk` planes so the two halo planes stay a small overhead
-  const int waves = tune_int("FVLB_WAVES", 8);
+  const int waves = tune_int("FVLB_WAVES", L::D == 2 ? 4 : 8);
   const int min_chunk = tune_int("FVLB_MIN_CHUNK", 8);
-  const long long target = (long long)std::max(d.sms, 1) * 2 * waves;
+  const long long target = (long long)std::max(d.sms, 1) * MINB * waves;
   int nchunk = (int)std::max<long long>(1, target / std::max(1, bx * by));
   int mchunk = std::max(min_chunk, (nm + nchunk - 1) / nchunk);
   mchunk = std::min(mchunk, nm);
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
-  k_step_fused<L, S, TX, (L::D == 2 ? 1 : TY), HOLD_H, MINB>
-      <<<grid, TX * (L::D == 2 ? 1 : TY), 0, d.stream>>>(g, ph, b, mchunk);
+  k_step_fused<L, S, GX, TY, MINB><<<grid, GX * TY * L::C * 32, 0, d.stream>>>(g, ph, b, mchunk);
   return cudaGetLastError();
 }
 
@@ -91,23 +83,20 @@ cudaError_t step_impl(const StepDesc& d) {
             static_cast<const S*>(d.h_in), static_cast<S*>(d.h_out),
             static_cast<X*>(d.chi)};
   if (d.variant == 0) {
+    // Shapes measured fastest on GB300 (256^3 D3Q19, 2048^2 D2Q9): 2D four
+    // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D 32 x 2
+    // nodes x 6 components (384 threads).  FVLB_TILE selects the others.
     const int cfg = tune_int("FVLB_TILE", 0);
+    constexpr bool wide = sizeof(RT<S>) == 8;
+    constexpr bool narrow = sizeof(S) == 2;
     if constexpr (L::D == 2) {
-      switch (cfg) {
-        case 1: return launch_fused<L, S, 128, 1, true, 4>(d, g, ph, b);
-        case 2: return launch_fused<L, S, 256, 1, true, 2>(d, g, ph, b);
-        case 3: return launch_fused<L, S, 64, 1, true, 8>(d, g, ph, b);
-        case 4: return launch_fused<L, S, 128, 1, false, 6>(d, g, ph, b);
-        default: return launch_fused<L, S, 128, 1, true, 1>(d, g, ph, b);
-      }
+      if (cfg == 1) return launch_fused<L, S, 2, 1, 3>(d, g, ph, b);
+      if constexpr (wide) return launch_fused<L, S, 4, 1, 1>(d, g, ph, b);
+      else return launch_fused<L, S, 4, 1, 2>(d, g, ph, b);
     } else {
-      switch (cfg) {
-        case 1: return launch_fused<L, S, 32, 4, true, 2>(d, g, ph, b);
-        case 2: return launch_fused<L, S, 32, 2, true, 4>(d, g, ph, b);
-        case 3: return launch_fused<L, S, 32, 8, false, 2>(d, g, ph, b);
-        case 4: return launch_fused<L, S, 32, 4, true, 1>(d, g, ph, b);
-        default: return launch_fused<L, S, 32, 8, true, 1>(d, g, ph, b);
-      }
+      if (cfg == 1) return launch_fused<L, S, 1, 4, 1>(d, g, ph, b);
+      if constexpr (narrow) return launch_fused<L, S, 1, 2, 2>(d, g, ph, b);
+      else return launch_fused<L, S, 1, 2, 1>(d, g, ph, b);
     }
   } else {
     const int threads = 128;

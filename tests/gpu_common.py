@@ -66,14 +66,14 @@ def compare(pr, steps, precision, tol, kernel=0, chunks=1, fields=("u", "p", "ta
         # a plain relative norm would amplify):
         #  - p is recovered as c_s^2/(1 - w_0) sum_{i!=0} f_i + ..., a sum of
         #    populations of size |u|, so its error is measured against
-        #    max(||p||, 0.1 ||u||);
+        #    max(||p||, ||u||);
         #  - tau_p = (eta_p/lambda)(A - I) is formed by the oracle from its
         #    full-tensor A (stored as h ~ w_i A), whose rounding is relative to
         #    ||A||, so its error is measured against
-        #    max(||tau_p||, 1e-2 (eta_p/lambda) ||A||).
+        #    max(||tau_p||, 0.1 (eta_p/lambda) ||A||).
         un = np.linalg.norm(ref["u"])
-        tfloor = 1e-2 * pr.eta_p / pr.lam * np.linalg.norm(ref["A"]) + 1e-30
-        floors = dict(u=1e-30, p=0.1 * un + 1e-30, tau_p=tfloor, A=1.0)
+        tfloor = 0.1 * pr.eta_p / pr.lam * np.linalg.norm(ref["A"]) + 1e-30
+        floors = dict(u=1e-30, p=un + 1e-30, tau_p=tfloor, A=1.0)
         for k in fields:
             worst[k] = max(worst[k], rel_l2(got[k], ref[k], floors[k]))
     s.close()
