@@ -135,6 +135,16 @@ def tgv_problem(n):
     return W.taylor_green_3d(n=n, U0=w["U0"], Re=w["Re"], Wi=w["Wi"], beta=w["beta"])
 
 
+def main_problem(args):
+    """The timed workload: the default D3Q19 Taylor-Green box, or (for
+    profiling and other forms) another size or the D2Q9 four-roll mill."""
+    from paper_2506_13072_gb300 import workloads as W
+
+    if args.lattice == "d2q9":
+        return W.four_roll(n=args.n or 2048, Wi=0.5, beta=0.5)
+    return tgv_problem(args.n or WORKLOAD["n"])
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle, timed on a bounded sample of the workload
 # ---------------------------------------------------------------------------
@@ -180,7 +190,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict("oracle sample 32^3"),
+        "data": "synthetic", "config": config_dict(args, "oracle sample 32^3"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -188,11 +198,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(note=""):
+def config_dict(args=None, note=""):
     w = WORKLOAD
-    return {"workload": f"D3Q19 Taylor-Green vortex {w['n']}^3 periodic, Re={w['Re']:g}, "
-                        f"Wi={w['Wi']:g}, beta={w['beta']:g}, u0={w['U0']:g}, FP32 fused step",
-            "lattice": w["lattice"], "grid": [w["n"]] * 3, "precision": "fp32",
+    prec = args.precision if args else "fp32"
+    if args is not None and args.lattice == "d2q9":
+        n = args.n or 2048
+        return {"workload": f"D2Q9 four-roll mill {n}^2 periodic, Wi=0.5, beta=0.5, {prec} fused step",
+                "lattice": "D2Q9", "grid": [n, n], "precision": prec, "kernel": "fused",
+                "parallelism": "replicas", "note": note}
+    n = (args.n if args is not None and args.n else w["n"])
+    return {"workload": f"D3Q19 Taylor-Green vortex {n}^3 periodic, Re={w['Re']:g}, "
+                        f"Wi={w['Wi']:g}, beta={w['beta']:g}, u0={w['U0']:g}, {prec} fused step",
+            "lattice": w["lattice"], "grid": [n] * 3, "precision": prec,
             "kernel": "fused", "l2": "state 18 GB >> 129 MB L2; no flush needed",
             "parallelism": "replicas", "note": note}
 
@@ -239,8 +256,9 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     F.use_torch_allocator()
     stream = torch.cuda.current_stream()
-    pr = tgv_problem(WORKLOAD["n"])
-    sim = F.Simulation.from_problem(pr, precision=F.FVLB_FP32, kernel=F.FVLB_KERNEL_FUSED,
+    pr = main_problem(args)
+    prec = F.PRECISIONS[args.precision]
+    sim = F.Simulation.from_problem(pr, precision=prec, kernel=F.FVLB_KERNEL_FUSED,
                                     stream=stream)
     sim.init_fields(pr.u0, pr.p0, pr.A0)
     sim.step(args.warmup)
@@ -266,18 +284,19 @@ def run_ours(args, rank, world, dist):
     achieved = bpu * sites / launch_s / 1e9    # GB/s, algorithmic bytes
     peaks, which = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    tr = traffic_record("tgv256_fp32_fused")
+    tr = traffic_record(f"{args.lattice}_{args.n or 'default'}_{args.precision}_fused")
 
     # end to end through the public API, host buffers: upload of the initial
     # fields, K steps, download of the velocity field, all inside the region
-    u0 = np.ascontiguousarray(pr.u0)
-    p0 = np.ascontiguousarray(pr.p0)
-    A0 = np.ascontiguousarray(F.full_to_compact(np.broadcast_to(np.eye(3), pr.shape + (3, 3))))
+    D = pr.D
+    u0 = np.ascontiguousarray(pr.u0 if pr.u0 is not None else np.zeros(pr.shape + (D,)))
+    p0 = np.ascontiguousarray(pr.p0 if pr.p0 is not None else np.zeros(pr.shape))
+    A0 = np.ascontiguousarray(F.full_to_compact(np.broadcast_to(np.eye(D), pr.shape + (D, D))))
     e2e_steps = args.steps
-    sim = F.Simulation.from_problem(pr, precision=F.FVLB_FP32, stream=stream)
+    sim = F.Simulation.from_problem(pr, precision=prec, stream=stream)
     sim.init_fields(u0, p0, A0)
     sim.step(2)
-    out = np.empty(sites * 3)
+    out = np.empty(sites * D)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.init_fields(u0, p0, A0)
@@ -289,7 +308,7 @@ def run_ours(args, rank, world, dist):
     d2h = out.nbytes / e2e_steps
 
     forms = {}
-    if not args.no_forms and rank == 0:
+    if not args.no_forms and rank == 0 and args.lattice == "d3q19" and not args.n:
         K = max(5, min(args.steps, 20))
         for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("bf16_dev", F.FVLB_BF16_DEV),
                            ("fp64", F.FVLB_FP64)):
@@ -314,9 +333,10 @@ def run_ours(args, rank, world, dist):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.precision, "f32 (16-bit storage)"),
         "data": "synthetic (seeded Taylor-Green initial field of Sec. 3.4)",
-        "config": config_dict(),
+        "config": config_dict(args),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": tr["dram_bytes_per_launch"] if tr else None,
@@ -343,6 +363,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--lattice", default="d3q19", choices=["d3q19", "d2q9"])
+    ap.add_argument("--n", type=int, default=0, help="grid nodes per axis (0: the default workload)")
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp64", "fp32", "fp16_dev", "bf16_dev", "fp16_dev_sr", "bf16_dev_sr"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

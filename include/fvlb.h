@@ -116,7 +116,8 @@ int fvlb_set_allocator(fvlb_alloc_fn alloc_fn, fvlb_free_fn free_fn, void *ctx);
 
 /* Create a simulation on the current CUDA device.
  *   lattice   FVLB_D2Q9 or FVLB_D3Q19
- *   nx,ny,nz  grid size, each >= 1 (nz is ignored and taken as 1 in 2D)
+ *   nx,ny,nz  grid size, each >= 1 (nz is ignored and taken as 1 in 2D);
+ *             Q * N must stay below 2^32 (N <= ~226 M sites for D3Q19)
  *   tau_s     flow relaxation time tau_f = nu_s / c_s^2 + 1/2 (Sec. 2.2);
  *             must be > 0.5
  *   eta_p     polymer viscosity mu_p = nu_p (rho_0 = 1), >= 0 (Sec. 2.1)

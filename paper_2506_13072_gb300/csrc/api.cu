@@ -340,8 +340,10 @@ int fvlb_create(fvlb_t* out, int lattice, int nx, int ny, int nz, double tau_s,
   if (lattice == FVLB_D2Q9) nz = 1;
   if (nx < 1 || ny < 1 || nz < 1)
     return fail(nullptr, FVLB_EINVAL, "fvlb_create: grid sizes must be >= 1");
-  if ((long long)nx * ny * nz > (1ll << 31))
-    return fail(nullptr, FVLB_EINVAL, "fvlb_create: more than 2^31 sites");
+  // population arrays are addressed with 32-bit element offsets: Q * pitch
+  // must stay below 2^32 (about 226 M sites for D3Q19, 477 M for D2Q9)
+  if ((long long)lattice * (((long long)nx * ny * nz + 63) / 64 * 64) >= (1ll << 32))
+    return fail(nullptr, FVLB_EINVAL, "fvlb_create: grid too large for one handle");
   if (!(tau_s > 0.5) || !std::isfinite(tau_s))
     return fail(nullptr, FVLB_EINVAL, "fvlb_create: tau_s must be > 0.5");
   if (!(lambda > 0.0) || !std::isfinite(lambda))

@@ -256,7 +256,7 @@ struct Split {
   static constexpr int NFMAX = (L::Q + L::C - 1) / L::C;
 };
 
-template <class L, class S, int GX, int TY, int MINB>
+template <class L, class S, int GX, int TY, int MINB, bool WALLS>
 __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
     k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
   using R = RT<S>;
@@ -278,9 +278,9 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
 
   const int nx = g.nx, ny = g.ny;
   const int nm = (D == 3) ? g.nz : g.ny;
-  const bool wall_x = g.walls & 1;
-  const bool wall_y = (D == 3) && ((g.walls >> 1) & 1);
-  const bool wall_m = (g.walls >> (D - 1)) & 1;
+  const bool wall_x = WALLS && (g.walls & 1);
+  const bool wall_y = WALLS && (D == 3) && ((g.walls >> 1) & 1);
+  const bool wall_m = WALLS && ((g.walls >> (D - 1)) & 1);
   const int x0 = blockIdx.x * TXS;
   const int y0 = (D == 3) ? blockIdx.y * TY : 0;
   const int m0 = blockIdx.z * mchunk;
@@ -300,6 +300,17 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
   const int y = (D == 3) ? y0 + ty : 0;
   const bool active = (x < nx) && (D == 2 || y < ny);
   const int e_own = (D == 3) ? (ty + 1) * EX + tx + 1 : tx + 1;
+  // this thread's component arrays; offsets within them are 32-bit
+  // (Q * pitch < 2^32 is checked at creation)
+  const S* __restrict__ hin_k = b.h_in + (long long)k * Q * P;
+  S* __restrict__ hout_k = b.h_out + (long long)k * Q * P;
+  const uint32_t P32 = (uint32_t)P;
+
+  // periodic neighbour offsets along x and y (constant over the march)
+  const int ox_p = (x == nx - 1) ? -(nx - 1) : 1;
+  const int ox_m = (x == 0) ? (nx - 1) : -1;
+  const int oy_p = (D == 3) ? ((y == ny - 1) ? -(ny - 1) * nx : nx) : 0;
+  const int oy_m = (D == 3) ? ((y == 0) ? (ny - 1) * nx : -nx) : 0;
 
   // ring slot of this thread (if tid < NE)
   int fgx = 0, fgy = 0;
@@ -366,15 +377,16 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
     if (do_fill) load_f<L, S>(b.f_in, P, slot_site(mn), fn);
     R hv[Q], fo[NFM];
     R old = R(0);
+    const uint32_t s32 = (uint32_t)s;
     if (active) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) hv[i] = load_h<L, S>(b.h_in, P, s, k, i);
+      for (int i = 0; i < Q; ++i) hv[i] = Store<S>::ld(hin_k + ((uint32_t)i * P32 + s32));
 #pragma unroll
       for (int j = 0; j < NFM; ++j) {
         const int i = k + j * C;
-        fo[j] = i < Q ? Store<S>::ld(b.f_in + i * P + s) : R(0);
+        fo[j] = i < Q ? Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s32)) : R(0);
       }
-      old = R(b.chi[k * P + s]);
+      old = R(b.chi[(uint32_t)k * P32 + s32]);
     }
     if (tid < NE) {
       if (do_fill) fill_u(fn, mn, rp);
@@ -465,43 +477,43 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
         A_k = Akk[q];
       }
       if (ph.first) old = chi_k;
-      b.chi[k * P + s] = X(chi_k);
+      b.chi[(uint32_t)k * P32 + s32] = X(chi_k);
       const R src = R(1.5) * chi_k - R(0.5) * old;
       uint32_t rng = Store<S>::sr
                          ? hash32(((uint32_t)s * 8u + (uint32_t)k) * 0x9e3779b9u ^ hash32(ph.step))
                          : 0u;
 
-      // per-site neighbour offsets along each axis (periodic wrap)
-      const long long strd[3] = {1, nx, (long long)nx * ny};
-      const int cz_ = (D == 3) ? m : 0;
-      const int pos[3] = {x, D == 3 ? y : m, cz_};
-      const int ext[3] = {nx, ny, g.nz};
-      long long offp[3], offm[3];
-      bool edgep[3], edgem[3];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        edgep[a] = pos[a] == ext[a] - 1;
-        edgem[a] = pos[a] == 0;
-        offp[a] = edgep[a] ? -(long long)(ext[a] - 1) * strd[a] : strd[a];
-        offm[a] = edgem[a] ? (long long)(ext[a] - 1) * strd[a] : -strd[a];
-      }
-      // destination of direction i: neighbour, or own node through a wall
-      auto dest = [&](int i, int& j) -> long long {
-        long long d = s;
+      // neighbour offsets along the march axis (periodic wrap)
+      const int strm = (D == 3) ? nx * ny : nx;
+      const int om_p = (m == nm - 1) ? -(nm - 1) * strm : strm;
+      const int om_m = (m == 0) ? (nm - 1) * strm : -strm;
+      const int opos[3] = {ox_p, D == 3 ? oy_p : om_p, om_p};
+      const int oneg[3] = {ox_m, D == 3 ? oy_m : om_m, om_m};
+      const int posv[3] = {x, D == 3 ? y : m, m};
+      const int extv[3] = {nx, D == 3 ? ny : nm, nm};
+      // destination of direction i (32-bit offset within a population
+      // array): the neighbour, or the own node through a halfway-bounce-back
+      // wall (direction reversed)
+      auto dest = [&](int i, int& j) -> uint32_t {
+        int d = (int)s32;
         bool bb = false;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const int c = cc<L>(i, a);
           if (c == 1) {
-            d += offp[a];
-            bb |= ((g.walls >> a) & 1) && edgep[a];
+            d += opos[a];
+            if (WALLS) bb |= ((g.walls >> a) & 1) && posv[a] == extv[a] - 1;
           } else if (c == -1) {
-            d += offm[a];
-            bb |= ((g.walls >> a) & 1) && edgem[a];
+            d += oneg[a];
+            if (WALLS) bb |= ((g.walls >> a) & 1) && posv[a] == 0;
           }
         }
-        j = bb ? L::opp(i) : i;
-        return bb ? s : d;
+        if (WALLS && bb) {
+          j = L::opp(i);
+          return s32;
+        }
+        j = i;
+        return (uint32_t)d;
       };
 
       // h_k: h* = (1 - 1/tau_h) h + w_i [alpha + c_i.u beta] with
@@ -521,8 +533,8 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
         }
         const R post = keep * hv[i] + R(L::w(i)) * (alpha + cu * beta);
         int j;
-        const long long d = dest(i, j);
-        store_h<L, S>(b.h_out, P, d, k, j, post, Store<S>::sr ? lcg_next(rng) : 0u);
+        const uint32_t d = dest(i, j);
+        Store<S>::st(hout_k + ((uint32_t)j * P32 + d), post, Store<S>::sr ? lcg_next(rng) : 0u);
       }
 
       // f_i, i = k (mod C): f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
@@ -546,8 +558,8 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
           const R fBi = fB_dir<L, R>(i, Ad, kB);
           const R post = fo[jj] - (fo[jj] - feq) * ph.inv_tau_f + fBi + Fi;
           int j;
-          const long long d = dest(i, j);
-          Store<S>::st(b.f_out + j * P + d, post, Store<S>::sr ? lcg_next(rng) : 0u);
+          const uint32_t d = dest(i, j);
+          Store<S>::st(b.f_out + ((uint32_t)j * P32 + d), post, Store<S>::sr ? lcg_next(rng) : 0u);
         }
       }
     }

@@ -69,7 +69,12 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   mchunk = std::min(mchunk, nm);
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
-  k_step_fused<L, S, GX, TY, MINB><<<grid, GX * TY * L::C * 32, 0, d.stream>>>(g, ph, b, mchunk);
+  if (d.walls)
+    k_step_fused<L, S, GX, TY, MINB, true>
+        <<<grid, GX * TY * L::C * 32, 0, d.stream>>>(g, ph, b, mchunk);
+  else
+    k_step_fused<L, S, GX, TY, MINB, false>
+        <<<grid, GX * TY * L::C * 32, 0, d.stream>>>(g, ph, b, mchunk);
   return cudaGetLastError();
 }
 
@@ -85,16 +90,13 @@ cudaError_t step_impl(const StepDesc& d) {
   if (d.variant == 0) {
     // Shapes measured fastest on GB300 (256^3 D3Q19, 2048^2 D2Q9): 2D four
     // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D 32 x 2
-    // nodes x 6 components (384 threads).  FVLB_TILE selects the others.
-    const int cfg = tune_int("FVLB_TILE", 0);
+    // nodes x 6 components (384 threads).
     constexpr bool wide = sizeof(RT<S>) == 8;
     constexpr bool narrow = sizeof(S) == 2;
     if constexpr (L::D == 2) {
-      if (cfg == 1) return launch_fused<L, S, 2, 1, 3>(d, g, ph, b);
       if constexpr (wide) return launch_fused<L, S, 4, 1, 1>(d, g, ph, b);
       else return launch_fused<L, S, 4, 1, 2>(d, g, ph, b);
     } else {
-      if (cfg == 1) return launch_fused<L, S, 1, 4, 1>(d, g, ph, b);
       if constexpr (narrow) return launch_fused<L, S, 1, 2, 2>(d, g, ph, b);
       else return launch_fused<L, S, 1, 2, 1>(d, g, ph, b);
     }
@@ -144,6 +146,16 @@ cudaError_t reduce_impl(const StepDesc& d, double* part, double* out) {
   if (e != cudaSuccess) return e;
   return reduce_finalize(part, nparts, d.N, out, d.stream);
 }
+
+// step_impl is instantiated per (lattice, storage) in its own translation
+// unit (k_step_<lattice>_<storage>.cu) so that the library builds in parallel.
+#define FVLB_EXTERN_STEP(L)                                                   \
+  extern template cudaError_t step_impl<L, double>(const StepDesc&);        \
+  extern template cudaError_t step_impl<L, float>(const StepDesc&);         \
+  extern template cudaError_t step_impl<L, __half>(const StepDesc&);        \
+  extern template cudaError_t step_impl<L, __nv_bfloat16>(const StepDesc&); \
+  extern template cudaError_t step_impl<L, half_sr>(const StepDesc&);       \
+  extern template cudaError_t step_impl<L, bf16_sr>(const StepDesc&);
 
 #define FVLB_DISPATCH(storage, CALL)                              \
   switch (storage) {                                              \

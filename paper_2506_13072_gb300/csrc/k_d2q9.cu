@@ -5,6 +5,8 @@
 
 namespace fvlb {
 
+FVLB_EXTERN_STEP(D2Q9)
+
 cudaError_t step_d2q9(const StepDesc& d) {
 #define CALL(S) step_impl<D2Q9, S>(d)
   FVLB_DISPATCH(d.storage, CALL)

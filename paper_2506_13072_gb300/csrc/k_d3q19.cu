@@ -5,6 +5,8 @@
 
 namespace fvlb {
 
+FVLB_EXTERN_STEP(D3Q19)
+
 cudaError_t step_d3q19(const StepDesc& d) {
 #define CALL(S) step_impl<D3Q19, S>(d)
   FVLB_DISPATCH(d.storage, CALL)
