@@ -179,6 +179,39 @@ int fvlb_fields(fvlb_t h, int which, double *host_out, size_t count);
  * Returns FVLB_EUNSTABLE (with out filled) if out[6] > 0. */
 int fvlb_reduce(fvlb_t h, double out[8]);
 
+/* The diagnostics of fvlb_reduce for a state the caller holds in its own
+ * device memory, with no device allocation at all.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory, such as code running inside a framework whose allocator
+ * has reserved the GPU's memory for itself, or an asynchronous pipeline
+ * that must not call cudaMalloc / cudaFree because they can synchronise
+ * the device.
+ *   lattice, storage  FVLB_D2Q9 / FVLB_D3Q19 and an FVLB_FP64 ... storage
+ *   nx, ny, nz        grid (nz ignored in 2D); N = nx ny nz
+ *   f                 device array f[Q][pitch] of the storage type
+ *   h                 device array h'[C][Q][pitch], h' = h - w_i delta_ab
+ *                     (the layout of fvlb_save_state's image after its
+ *                     64-byte header)
+ *   pitch             elements between population arrays, >= N
+ *   eta_p, lambda     polymer viscosity and relaxation time (PE = tr tau_p/2)
+ *   F                 host array of the uniform body force entering
+ *                     u = sum c_i f_i + F/2, or NULL for 0
+ *   out               device array of 8 doubles, filled as by fvlb_reduce
+ *                     (no FVLB_EUNSTABLE check: read out[6])
+ *   stream            cudaStream_t, or NULL for the legacy default stream
+ * The work is enqueued on `stream` and the call returns without waiting.
+ * Scratch: the per-block partial sums live in a file-scope device array of
+ * 1024 x 8 doubles (64 KiB) that every GPU using the library keeps until
+ * the process exits; N beyond the library's limit is rejected with
+ * FVLB_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the array: calls whose kernels overlap on the
+ * GPU race and give wrong results. */
+int fvlb_reduce_noalloc(int lattice, int storage, int nx, int ny, int nz,
+                        const void *f, const void *h, long long pitch,
+                        double eta_p, double lambda, const double F[3],
+                        double *out, void *stream);
+
 /* Wait for all GPU work of the handle. */
 int fvlb_synchronize(fvlb_t h);
 

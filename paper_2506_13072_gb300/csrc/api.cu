@@ -276,37 +276,14 @@ size_t state_bytes(fvlb_t h) {
 
 namespace fvlb {
 
+int set_global_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+
 int reduce_parts(long long N) {
   const long long want = (N + kReduceThreads - 1) / kReduceThreads;
   return (int)std::max<long long>(1, std::min<long long>(want, 1024));
-}
-
-__global__ void __launch_bounds__(kReduceThreads)
-    k_reduce_final(const double* __restrict__ part, int nparts, long long nsites,
-                   double* __restrict__ out) {
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double v = part[p * 8 + q];
-      acc[q] = q == 7 ? fmax(acc[q], v) : acc[q] + v;
-    }
-  }
-  __shared__ double sm[kReduceThreads / 32][8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const double v = q == 7 ? warp_max(acc[q]) : warp_sum(acc[q]);
-    if (lane == 0) sm[wid][q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    const int q = threadIdx.x;
-    double v = sm[0][q];
-    for (int w = 1; w < kReduceThreads / 32; ++w) v = q == 7 ? fmax(v, sm[w][q]) : v + sm[w][q];
-    if (q == 4 || q == 5) v /= (double)nsites;
-    out[q] = v;
-  }
 }
 
 cudaError_t reduce_finalize(const double* part, int nparts, long long N, double* out,

@@ -61,5 +61,7 @@ cudaError_t reduce_d2q9(const StepDesc& d, double* part, double* out);
 cudaError_t reduce_d3q19(const StepDesc& d, double* part, double* out);
 cudaError_t reduce_finalize(const double* part, int nparts, long long N, double* out,
                             cudaStream_t stream);
+// record the message returned by fvlb_last_error(NULL); returns code
+int set_global_error(int code, const char* msg);
 
 }  // namespace fvlb

@@ -96,6 +96,10 @@ _SIGS = {
     "fvlb_load_state": ([_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     "fvlb_bytes_per_update": ([_H, _dp], ctypes.c_int),
     "fvlb_last_error": ([_H], ctypes.c_char_p),
+    "fvlb_reduce_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
+                             ctypes.c_double, _dp, ctypes.c_void_p, ctypes.c_void_p],
+                            ctypes.c_int),
     "fvlb_destroy": ([_H], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
