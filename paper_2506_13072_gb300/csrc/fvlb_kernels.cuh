@@ -243,11 +243,13 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
 // Q (1 + C) keeps the register footprint low enough for many resident warps.
 //
 // Velocity gradient: the same-step velocity of the tile and a one-node halo
-// is kept in a three-plane shared-memory ring (planes m-1, m, m+1), filled
-// from the populations of each plane one iteration ahead; halo velocities
-// are recomputed from their populations (read through L2), so blocks never
-// wait on each other.  Per plane: one memory phase (the ring fill of plane
-// m+1 and the collision loads of plane m are issued together), two barriers.
+// is kept in a four-plane shared-memory ring (planes m-1 .. m+2).  Separate
+// fill warps compute it from the populations of plane m+2 while the
+// collision warps update plane m, so the fill's memory latency hides behind
+// the collision; halo velocities are recomputed from their populations (read
+// through L2), so blocks never wait on each other.  Per plane: the collision
+// warps' memory phase, barrier, collision phase (with the fill running),
+// barrier.
 // ---------------------------------------------------------------------------
 template <class L>
 struct Split {
@@ -256,23 +258,34 @@ struct Split {
   static constexpr int NFMAX = (L::Q + L::C - 1) / L::C;
 };
 
-template <class L, class S, int GX, int TY, int MINB, bool WALLS>
-__global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
+// FW: dedicated fill warps computing the ring one plane ahead (D3Q19, where
+// a halo velocity costs 19 loads), or the ring filled by the first NE
+// collision threads in their own memory phase (D2Q9, 9 loads).
+template <class L, int GX, int TY, bool FW>
+struct FusedShape {
+  static constexpr int NG = GX * TY;              // groups of 32 nodes per plane tile
+  static constexpr int NCW = NG * L::C;           // collision warps
+  static constexpr int TXS = GX * 32;             // tile extent along x
+  static constexpr int EX = TXS + 2;
+  static constexpr int EY = (L::D == 3) ? TY + 2 : 1;
+  static constexpr int NE = EX * EY;              // ring slots per plane
+  static constexpr int NFW = FW ? (NE + 31) / 32 : 0;  // fill warps
+  static constexpr int NT = (NCW + NFW) * 32;     // threads
+};
+
+template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW>
+__global__ void __launch_bounds__(FusedShape<L, GX, TY, FW>::NT, MINB)
     k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
   using R = RT<S>;
   using X = typename Store<S>::X;
+  using Sh = FusedShape<L, GX, TY, FW>;
   constexpr int D = L::D, Q = L::Q, C = L::C;
-  constexpr int NG = GX * TY;           // groups of 32 nodes per plane tile
-  constexpr int NT = NG * C * 32;       // threads
-  constexpr int TXS = GX * 32;          // tile extent along x
-  constexpr int EX = TXS + 2;
-  constexpr int EY = (D == 3) ? TY + 2 : 1;
-  constexpr int NE = EX * EY;           // ring slots per plane
+  constexpr int NG = Sh::NG, NCW = Sh::NCW, TXS = Sh::TXS, EX = Sh::EX, NE = Sh::NE;
   constexpr int NS = NG * 32;           // nodes per plane tile
   constexpr int NFM = Split<L>::NFMAX;
   static_assert(D == 3 || TY == 1, "2D tiles are one row high");
-  static_assert(NE <= NT, "one ring slot per thread at most");
-  __shared__ R ring[3][D][NE];
+  static_assert(FW || NE <= NCW * 32, "in-collision fill: one ring slot per thread");
+  __shared__ R ring[4][D][NE];          // velocity of planes m-1 .. m+2
   __shared__ R sAd[C][NS];              // A - I of the tile nodes
   __shared__ R sPf[C][NS];              // partial sums of f_{i != 0}
 
@@ -286,10 +299,83 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
   const int m0 = blockIdx.z * mchunk;
   const int m1 = min(m0 + mchunk, nm);
   const long long P = g.pitch;
+  const uint32_t P32 = (uint32_t)P;
 
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
   const int warp = tid >> 5;
+  const bool filler = warp >= NCW;      // fill warps: ring only
+  auto slot = [&](int q) { return (q - m0 + 1) & 3; };
+  auto plane_of = [&](int q) -> int {  // -1: beyond a wall
+    if (q < 0 || q >= nm) return wall_m ? -1 : (q + nm) % nm;
+    return q;
+  };
+
+  // ring slot e of a plane: its node, or none beyond a wall
+  auto slot_node = [&](int e, int& gx, int& gy) -> bool {
+    if (e >= NE) return false;
+    const int ex = e % EX, ey = e / EX;
+    gx = x0 + ex - 1;
+    gy = (D == 3) ? y0 + ey - 1 : 0;
+    if (gx < 0 || gx >= nx) {
+      if (wall_x) return false;
+      gx = ((gx % nx) + nx) % nx;
+    }
+    if (D == 3 && (gy < 0 || gy >= ny)) {
+      if (wall_y) return false;
+      gy = ((gy % ny) + ny) % ny;
+    }
+    return true;
+  };
+  // velocity of ring slot e of plane q from its populations fv (loaded by
+  // the caller when `ok`), into the plane's ring slot
+  auto fill_store = [&](int e, bool ok, int mm, int gx, int gy, const R (&fv)[Q], int q) {
+    R u[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = R(0);
+    if (ok) {
+      R F[3];
+      body_force<L, R>(ph, gx, D == 3 ? gy : mm, F);
+      velocity<L, R>(fv, F, u);
+    }
+    const int r = slot(q);
+#pragma unroll
+    for (int a = 0; a < D; ++a) ring[r][a][e] = u[a];
+  };
+  auto fill = [&](int e, int q) {
+    if (e >= NE) return;
+    int gx = 0, gy = 0;
+    const bool has = slot_node(e, gx, gy);
+    const int mm = plane_of(q);
+    const bool ok = has && mm >= 0;
+    R fv[Q];
+    if (ok) {
+      const long long s = (D == 3) ? ((long long)mm * ny + gy) * nx + gx : (long long)mm * nx + gx;
+      load_f<L, S>(b.f_in, P, s, fv);
+    }
+    fill_store(e, ok, mm, gx, gy, fv, q);
+  };
+
+  if (FW && filler) {
+    // ---------------- fill warps ---------------------------------------------
+    const int e = tid - NCW * 32;
+    fill(e, m0 - 1);
+    fill(e, m0);
+    fill(e, m0 + 1);
+    __syncthreads();
+    for (int m = m0; m < m1; ++m) {
+      __syncthreads();               // A: collision loads of plane m done
+      if (m + 2 <= m1) fill(e, m + 2);  // overlaps the collision of plane m
+      __syncthreads();               // B
+    }
+    return;
+  }
+  if (!FW) {
+    fill(tid, m0 - 1);
+    fill(tid, m0);
+  }
+
+  // ---------------- collision warps ------------------------------------------
+  const int lane = tid & 31;
   const int grp = warp / C;
   const int k = warp - grp * C;         // stress component of this thread
   const int gxi = grp % GX, gyi = grp / GX;
@@ -304,80 +390,34 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
   // (Q * pitch < 2^32 is checked at creation)
   const S* __restrict__ hin_k = b.h_in + (long long)k * Q * P;
   S* __restrict__ hout_k = b.h_out + (long long)k * Q * P;
-  const uint32_t P32 = (uint32_t)P;
-
   // periodic neighbour offsets along x and y (constant over the march)
   const int ox_p = (x == nx - 1) ? -(nx - 1) : 1;
   const int ox_m = (x == 0) ? (nx - 1) : -1;
   const int oy_p = (D == 3) ? ((y == ny - 1) ? -(ny - 1) * nx : nx) : 0;
   const int oy_m = (D == 3) ? ((y == 0) ? (ny - 1) * nx : -nx) : 0;
-
-  // ring slot of this thread (if tid < NE)
-  int fgx = 0, fgy = 0;
-  bool fok = tid < NE;
-  if (fok) {
-    const int ex = tid % EX, ey = tid / EX;
-    fgx = x0 + ex - 1;
-    fgy = (D == 3) ? y0 + ey - 1 : 0;
-    if (fgx < 0 || fgx >= nx) {
-      if (wall_x) fok = false;
-      else fgx = ((fgx % nx) + nx) % nx;
-    }
-    if (D == 3 && (fgy < 0 || fgy >= ny)) {
-      if (wall_y) fok = false;
-      else fgy = ((fgy % ny) + ny) % ny;
-    }
-  }
-  auto plane_of = [&](int m) -> int {  // -1: beyond a wall
-    if (m < 0 || m >= nm) return wall_m ? -1 : (m + nm) % nm;
-    return m;
-  };
-  auto slot_site = [&](int m) -> long long {
-    return (D == 3) ? ((long long)m * ny + fgy) * nx + fgx : (long long)m * nx + fgx;
-  };
-  auto fill_u = [&](const R (&fv)[Q], int m, int r) {
-    R u[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) u[a] = R(0);
-    R F[3];
-    body_force<L, R>(ph, fgx, D == 3 ? fgy : m, F);
-    velocity<L, R>(fv, F, u);
-#pragma unroll
-    for (int a = 0; a < D; ++a) ring[r][a][tid] = u[a];
-  };
-  auto fill_zero = [&](int r) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) ring[r][a][tid] = R(0);
-  };
-
-  // prologue: planes m0 - 1 and m0
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int mm = plane_of(m0 - 1 + q);
-    if (tid < NE) {
-      if (fok && mm >= 0) {
-        R fv[Q];
-        load_f<L, S>(b.f_in, P, slot_site(mm), fv);
-        fill_u(fv, mm, q);
-      } else {
-        fill_zero(q);
-      }
-    }
-  }
-  __syncthreads();
+  __syncthreads();                      // ring prologue
 
   for (int m = m0; m < m1; ++m) {
-    const int rm = (m - m0) % 3, rc = (m - m0 + 1) % 3, rp = (m - m0 + 2) % 3;
+    const int rm = slot(m - 1), rc = slot(m), rp = slot(m + 1);
     const long long s = (D == 3) ? ((long long)m * ny + y) * nx + x : (long long)m * nx + x;
+    const uint32_t s32 = (uint32_t)s;
 
-    // ---- memory phase: ring fill of plane m + 1 and this node's populations
+    // ---- memory phase: this node's populations of component k ---------------
+    // (without fill warps, the first NE threads also load the populations of
+    // their ring slot of plane m + 1)
+    int fgx = 0, fgy = 0;
     const int mn = plane_of(m + 1);
-    const bool do_fill = tid < NE && fok && mn >= 0;
-    R fn[Q];
-    if (do_fill) load_f<L, S>(b.f_in, P, slot_site(mn), fn);
+    const bool fslot = !FW && tid < NE;
+    const bool fok = fslot && slot_node(tid, fgx, fgy) && mn >= 0;
+    R fn[FW ? 1 : Q];
+    if (!FW && fok) {
+      const long long sn = (D == 3) ? ((long long)mn * ny + fgy) * nx + fgx
+                                    : (long long)mn * nx + fgx;
+#pragma unroll
+      for (int i = 0; i < (FW ? 1 : Q); ++i) fn[i] = Store<S>::ld(b.f_in + i * P + sn);
+    }
     R hv[Q], fo[NFM];
     R old = R(0);
-    const uint32_t s32 = (uint32_t)s;
     if (active) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) hv[i] = Store<S>::ld(hin_k + ((uint32_t)i * P32 + s32));
@@ -387,12 +427,6 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
         fo[j] = i < Q ? Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s32)) : R(0);
       }
       old = R(b.chi[(uint32_t)k * P32 + s32]);
-    }
-    if (tid < NE) {
-      if (do_fill) fill_u(fn, mn, rp);
-      else fill_zero(rp);
-    }
-    if (active) {
       R a = R(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) a += hv[i];
@@ -405,38 +439,16 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
       }
       sPf[k][node] = pf;
     }
-    __syncthreads();
+    if constexpr (!FW) {
+      if (fslot) fill_store(tid, fok, mn, fgx, fgy, fn, m + 1);
+    }
+    __syncthreads();                    // A
 
-    // ---- collision phase ----------------------------------------------------
+    // ---- collision phase ------------------------------------------------------
     if (active) {
-      R u[D], gr[D][D];
+      R u[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) u[a] = ring[rc][a][e_own];
-#pragma unroll
-      for (int bq = 0; bq < D; ++bq) {
-        const R uo = u[bq];
-        {
-          const R up = ring[rc][bq][e_own + 1], um = ring[rc][bq][e_own - 1];
-          R d = R(0.5) * (up - um);
-          if (wall_x && x == 0) d = uo + up * R(1.0 / 3.0);
-          if (wall_x && x == nx - 1) d = -(uo + um * R(1.0 / 3.0));
-          gr[0][bq] = d;
-        }
-        if (D == 3) {
-          const R up = ring[rc][bq][e_own + EX], um = ring[rc][bq][e_own - EX];
-          R d = R(0.5) * (up - um);
-          if (wall_y && y == 0) d = uo + up * R(1.0 / 3.0);
-          if (wall_y && y == ny - 1) d = -(uo + um * R(1.0 / 3.0));
-          gr[1][bq] = d;
-        }
-        {
-          const R up = ring[rp][bq][e_own], um = ring[rm][bq][e_own];
-          R d = R(0.5) * (up - um);
-          if (wall_m && m == 0) d = uo + up * R(1.0 / 3.0);
-          if (wall_m && m == nm - 1) d = -(uo + um * R(1.0 / 3.0));
-          gr[D - 1][bq] = d;
-        }
-      }
       R Ad[C];
 #pragma unroll
       for (int q = 0; q < C; ++q) Ad[q] = sAd[q][node];
@@ -459,10 +471,8 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
                   (sumf + R(-1.5 * w0) * uu + ph.tau_f * (R(-3.0 * w0) * ph.kf * Fu) +
                    ph.tau_f * fB0);
 
-      // stress source of this component (Sec. 2.3)
-      R Akk[C];
-#pragma unroll
-      for (int q = 0; q < C; ++q) Akk[q] = Ad[q] + (diag<L>(q) ? R(1) : R(0));
+      // stress source of this component (Sec. 2.3):
+      // chi_ab = -(A - I)_ab / lambda + sum_r (A_ar d_r u_b + d_r u_a A_rb)
       R chi_k = R(0), Ad_k = R(0), A_k = R(0);
 #pragma unroll
       for (int q = 0; q < C; ++q) {
@@ -470,11 +480,36 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
         const int a = L::ca(q), bb = L::cb(q);
         R v = -Ad[q] * ph.inv_lam;
 #pragma unroll
-        for (int r = 0; r < D; ++r)
-          v += Akk[sym<L>(a, r)] * gr[r][bb] + gr[r][a] * Akk[sym<L>(r, bb)];
+        for (int r = 0; r < D; ++r) {
+          // d_r u_a and d_r u_b from the ring (central, or one-sided at walls)
+          R dua, dub;
+          {
+            int e_p, e_m, r_p, r_m;
+            bool lo, hi;
+            if (r == 0) {
+              e_p = e_own + 1; e_m = e_own - 1; r_p = rc; r_m = rc;
+              lo = wall_x && x == 0; hi = wall_x && x == nx - 1;
+            } else if (r == 1 && D == 3) {
+              e_p = e_own + EX; e_m = e_own - EX; r_p = rc; r_m = rc;
+              lo = wall_y && y == 0; hi = wall_y && y == ny - 1;
+            } else {
+              e_p = e_own; e_m = e_own; r_p = rp; r_m = rm;
+              lo = wall_m && m == 0; hi = wall_m && m == nm - 1;
+            }
+            const R pa = ring[r_p][a][e_p], ma = ring[r_m][a][e_m];
+            const R pb = ring[r_p][bb][e_p], mb = ring[r_m][bb][e_m];
+            dua = R(0.5) * (pa - ma);
+            dub = R(0.5) * (pb - mb);
+            if (lo) { dua = u[a] + pa * R(1.0 / 3.0); dub = u[bb] + pb * R(1.0 / 3.0); }
+            if (hi) { dua = -(u[a] + ma * R(1.0 / 3.0)); dub = -(u[bb] + mb * R(1.0 / 3.0)); }
+          }
+          const R Aar = Ad[sym<L>(a, r)] + (a == r ? R(1) : R(0));
+          const R Arb = Ad[sym<L>(r, bb)] + (r == bb ? R(1) : R(0));
+          v += Aar * dub + dua * Arb;
+        }
         chi_k = v;
         Ad_k = Ad[q];
-        A_k = Akk[q];
+        A_k = Ad[q] + (diag<L>(q) ? R(1) : R(0));
       }
       if (ph.first) old = chi_k;
       b.chi[(uint32_t)k * P32 + s32] = X(chi_k);
@@ -563,7 +598,7 @@ __global__ void __launch_bounds__(GX* TY * L::C * 32, MINB)
         }
       }
     }
-    __syncthreads();
+    __syncthreads();                    // B
   }
 }
 

@@ -13,8 +13,9 @@ namespace fvlb {
 // Tile shapes of the fused step: GX x TY groups of 32 x-consecutive nodes
 // (a warp spans x, so every population load and store is one coalesced
 // 128-byte line, shifted by at most one element for the pushes), C threads
-// per node; MINB is the number of resident blocks per SM the register
-// allocation must allow.
+// per node, optional fill warps (FW); MINB is the number of resident blocks
+// per SM the register allocation must allow.  The shapes below were the
+// fastest of those measured on GB300 (256^3 D3Q19, 2048^2 D2Q9).
 // Launch-shape overrides from the environment, for tuning sweeps.
 inline int tune_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
@@ -52,7 +53,7 @@ inline int grid_stride_blocks(long long N, int threads, int sms) {
   return (int)std::max<long long>(1, std::min(want, cap));
 }
 
-template <class L, class S, int GX, int TY, int MINB>
+template <class L, class S, int GX, int TY, int MINB, bool FW>
 cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                          const Bufs<S>& b) {
   constexpr int TXS = GX * 32;
@@ -61,7 +62,7 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   const int nm = L::D == 3 ? g.nz : d.ny;
   // chunks along the march axis: enough blocks for several waves, but at
   // least `min_chunk` planes so the two halo planes stay a small overhead
-  const int waves = tune_int("FVLB_WAVES", L::D == 2 ? 4 : 8);
+  const int waves = tune_int("FVLB_WAVES", L::D == 2 ? 4 : 16);
   const int min_chunk = tune_int("FVLB_MIN_CHUNK", 8);
   const long long target = (long long)std::max(d.sms, 1) * MINB * waves;
   int nchunk = (int)std::max<long long>(1, target / std::max(1, bx * by));
@@ -69,12 +70,11 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   mchunk = std::min(mchunk, nm);
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
+  constexpr int NT = FusedShape<L, GX, TY, FW>::NT;
   if (d.walls)
-    k_step_fused<L, S, GX, TY, MINB, true>
-        <<<grid, GX * TY * L::C * 32, 0, d.stream>>>(g, ph, b, mchunk);
+    k_step_fused<L, S, GX, TY, MINB, true, FW><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
   else
-    k_step_fused<L, S, GX, TY, MINB, false>
-        <<<grid, GX * TY * L::C * 32, 0, d.stream>>>(g, ph, b, mchunk);
+    k_step_fused<L, S, GX, TY, MINB, false, FW><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
   return cudaGetLastError();
 }
 
@@ -92,13 +92,14 @@ cudaError_t step_impl(const StepDesc& d) {
     // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D 32 x 2
     // nodes x 6 components (384 threads).
     constexpr bool wide = sizeof(RT<S>) == 8;
-    constexpr bool narrow = sizeof(S) == 2;
     if constexpr (L::D == 2) {
-      if constexpr (wide) return launch_fused<L, S, 4, 1, 1>(d, g, ph, b);
-      else return launch_fused<L, S, 4, 1, 2>(d, g, ph, b);
+      // 4 groups x 3 components, ring filled by the collision threads
+      if constexpr (wide) return launch_fused<L, S, 4, 1, 1, false>(d, g, ph, b);
+      else return launch_fused<L, S, 4, 1, 2, false>(d, g, ph, b);
     } else {
-      if constexpr (narrow) return launch_fused<L, S, 1, 2, 2>(d, g, ph, b);
-      else return launch_fused<L, S, 1, 2, 1>(d, g, ph, b);
+      // 32 x 1 nodes x 6 components + 4 fill warps, two blocks per SM
+      if constexpr (wide) return launch_fused<L, S, 1, 1, 1, true>(d, g, ph, b);
+      else return launch_fused<L, S, 1, 1, 2, true>(d, g, ph, b);
     }
   } else {
     const int threads = 128;
