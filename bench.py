@@ -245,6 +245,36 @@ def form_rate(F, pr, precision, steps, warmup, stream, kernel=0):
             "bytes_per_update": bpu, "ms_per_step": round(1e3 * dt / steps, 4)}
 
 
+def batch_rate(F, precision, stream, steps=40):
+    """512 uneven D2Q9 instances (four-roll / Poiseuille, n log-uniform in
+    [32, 512], seed 0) in one persistent launch per step, graph-replayed,
+    tile shape autotuned (the tuning steps run before the timed region)."""
+    import torch
+
+    from paper_2506_13072_gb300 import workloads as W
+
+    probs = W.batch_instances(count=512, seed=0)
+    stream = torch.cuda.Stream()      # graph capture needs a non-legacy stream
+    bt = F.Batch(probs, precision=precision, stream=stream)
+    bt.step(1 + 18 + 2)        # first step, autotuning, one graph replay
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bt.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    info = bt.info()
+    bt.close()
+    sites = info["sites"]
+    return {"mlups": round(sites * steps / dt / 1e6, 1),
+            "gbs_algorithmic": round(info["bytes_per_update"] * sites * steps / dt / 1e9, 1),
+            "bytes_per_update": info["bytes_per_update"], "ms_per_step": round(1e3 * dt / steps, 4),
+            "sites": sites, "instances": 512, "tile": [32 * info["gx"], info["rows"]],
+            "launches_per_step": 1}
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -318,6 +348,10 @@ def run_ours(args, rank, world, dist):
         for name, prec in (("fp32", F.FVLB_FP32), ("fp16_dev", F.FVLB_FP16_DEV)):
             forms[f"d2q9_2048^2_four_roll_{name}"] = form_rate(F, pr2, prec, K, 2, stream)
         forms["d3q19_256^3_fp32_split"] = form_rate(F, pr, F.FVLB_FP32, K, 2, stream, kernel=1)
+        torch.cuda.empty_cache()
+        for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("fp32", F.FVLB_FP32)):
+            forms[f"batched_512_d2q9_{name}"] = batch_rate(F, prec, stream)
+            torch.cuda.empty_cache()
         for k, v in forms.items():
             v["frac_of_hbm_peak"] = round(v["gbs_algorithmic"] / peak, 3)
         torch.cuda.synchronize()

@@ -212,6 +212,61 @@ int fvlb_reduce_noalloc(int lattice, int storage, int nx, int ny, int nz,
                         double eta_p, double lambda, const double F[3],
                         double *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent D2Q9 grids (uneven sizes and parameters) in one
+ * object, advanced by ONE persistent kernel launch per step (each resident
+ * block walks a fixed list of tiles of all grids), the steps replayed from a
+ * captured CUDA graph.  The update of every node is the one of fvlb_step
+ * (Sec. 2.2-2.3); the arithmetic does not depend on the tile shape, which an
+ * autotuner picks by timing candidate shapes on the batch itself.
+ * ------------------------------------------------------------------------- */
+typedef struct fvlb_batch_s *fvlb_batch_t;
+
+typedef struct {
+  int nx, ny;          /* grid of this instance, >= 1 each */
+  double tau_s;        /* > 0.5 */
+  double eta_p;        /* >= 0 */
+  double lambda;       /* > 0 */
+  fvlb_force force;    /* body force (as for fvlb_create) */
+  unsigned walls;      /* bit 0: walls on x, bit 1: walls on y */
+} fvlb_instance;
+
+/* Create a batch of `count` D2Q9 instances (specs copied) with storage
+ * FVLB_FP64, FVLB_FP32, FVLB_FP16_DEV or FVLB_BF16_DEV; allocates all state
+ * (through the allocator hooks) and sets every instance to rest.  The batch
+ * owns a non-blocking stream until fvlb_batch_set_stream. */
+int fvlb_batch_create(fvlb_batch_t *out, int lattice, int count,
+                      const fvlb_instance *specs, int storage);
+
+/* Use a caller stream (non-NULL: graph capture needs a non-legacy stream). */
+int fvlb_batch_set_stream(fvlb_batch_t b, void *stream);
+
+/* Initial fields of instance `index` (layouts as fvlb_init_fields); only
+ * before the first step. */
+int fvlb_batch_init_fields(fvlb_batch_t b, int index, const double *u0,
+                           const double *p0, const double *A0);
+
+/* Advance every instance n steps.  The first step is launched directly; the
+ * first call with at least 18 further steps times 9 tile shapes over two real
+ * steps each (synchronising) and keeps the fastest; later pairs of steps
+ * replay a captured two-step graph. */
+int fvlb_batch_step(fvlb_batch_t b, long n);
+
+/* One field of instance `index` (as fvlb_fields), synchronising. */
+int fvlb_batch_fields(fvlb_batch_t b, int index, int which, double *host_out,
+                      size_t count);
+
+/* Total nodes, algorithmic bytes per node update, chosen tile shape (32 gx
+ * nodes x rows) and the tuned time per step in ms (0 before tuning); any
+ * pointer may be NULL. */
+int fvlb_batch_info(fvlb_batch_t b, long long *sites, double *bytes_per_update,
+                    int *gx, int *rows, double *tuned_ms_per_step);
+
+int fvlb_batch_synchronize(fvlb_batch_t b);
+int fvlb_batch_get_time(fvlb_batch_t b, long *t);
+const char *fvlb_batch_last_error(fvlb_batch_t b);
+int fvlb_batch_destroy(fvlb_batch_t b); /* NULL-safe */
+
 /* Wait for all GPU work of the handle. */
 int fvlb_synchronize(fvlb_t h);
 

@@ -281,6 +281,12 @@ int set_global_error(int code, const char* msg) {
   return code;
 }
 
+void current_allocator(fvlb_alloc_fn* a, fvlb_free_fn* f, void** ctx) {
+  *a = g_alloc;
+  *f = g_free;
+  *ctx = g_actx;
+}
+
 int reduce_parts(long long N) {
   const long long want = (N + kReduceThreads - 1) / kReduceThreads;
   return (int)std::max<long long>(1, std::min<long long>(want, 1024));

@@ -63,5 +63,10 @@ cudaError_t reduce_finalize(const double* part, int nparts, long long N, double*
                             cudaStream_t stream);
 // record the message returned by fvlb_last_error(NULL); returns code
 int set_global_error(int code, const char* msg);
+}  // namespace fvlb
+#include "fvlb.h"
+namespace fvlb {
+// the process-wide allocator hooks (NULL: cudaMalloc / cudaFree)
+void current_allocator(fvlb_alloc_fn* a, fvlb_free_fn* f, void** ctx);
 
 }  // namespace fvlb

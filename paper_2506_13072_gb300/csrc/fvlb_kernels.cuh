@@ -273,9 +273,13 @@ struct FusedShape {
   static constexpr int NT = (NCW + NFW) * 32;     // threads
 };
 
-template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW>
-__global__ void __launch_bounds__(FusedShape<L, GX, TY, FW>::NT, MINB)
-    k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
+// One tile of the fused step: tile (bx, by) of the plane, chunk bz of the
+// march axis.  Called by k_step_fused (one tile per block) and by the
+// batched persistent kernel (many tiles of many grids per block).
+template <class L, class S, int GX, int TY, bool WALLS, bool FW>
+__device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
+                                           const Bufs<S>& b, int mchunk, int bx, int by,
+                                           int bz) {
   using R = RT<S>;
   using X = typename Store<S>::X;
   using Sh = FusedShape<L, GX, TY, FW>;
@@ -294,9 +298,9 @@ __global__ void __launch_bounds__(FusedShape<L, GX, TY, FW>::NT, MINB)
   const bool wall_x = WALLS && (g.walls & 1);
   const bool wall_y = WALLS && (D == 3) && ((g.walls >> 1) & 1);
   const bool wall_m = WALLS && ((g.walls >> (D - 1)) & 1);
-  const int x0 = blockIdx.x * TXS;
-  const int y0 = (D == 3) ? blockIdx.y * TY : 0;
-  const int m0 = blockIdx.z * mchunk;
+  const int x0 = bx * TXS;
+  const int y0 = (D == 3) ? by * TY : 0;
+  const int m0 = bz * mchunk;
   const int m1 = min(m0 + mchunk, nm);
   const long long P = g.pitch;
   const uint32_t P32 = (uint32_t)P;
@@ -601,6 +605,70 @@ __global__ void __launch_bounds__(FusedShape<L, GX, TY, FW>::NT, MINB)
     __syncthreads();                    // B
   }
 }
+
+template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW>
+__global__ void __launch_bounds__(FusedShape<L, GX, TY, FW>::NT, MINB)
+    k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
+  fused_tile<L, S, GX, TY, WALLS, FW>(g, ph, b, mchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent step: many independent grids (instances) of one lattice
+// in one launch.  The host lists the tiles of every instance (instance, x
+// tile, march chunk); each resident block walks the list with a stride of
+// the grid size, so no block waits on another and the assignment is fixed
+// (deterministic).  Per-instance geometry, physics and array offsets come
+// from `inst`; the double buffers of all instances live in two arenas and
+// `parity` says which one holds the current state.  The step count is read
+// from device memory so that a captured CUDA graph can replay steps.
+// ---------------------------------------------------------------------------
+template <class S>
+struct BatchInst {
+  Grid g;
+  Phys<RT<S>> ph;          // first / step / Fv filled in per launch
+  long long f_off, h_off, chi_off;  // element offsets into the arenas
+  int cosine;              // F = F0 cos(omega t)
+  double F0[3];
+  double omega;
+};
+
+struct BatchTile {
+  int inst;
+  int bx;
+  int bz;
+};
+
+template <class L, class S, int GX, int MINB>
+__global__ void __launch_bounds__(FusedShape<L, GX, 1, false>::NT, MINB)
+    k_step_batched(const BatchInst<S>* __restrict__ inst, const BatchTile* __restrict__ tiles,
+                   int ntiles, S* fA, S* fB, S* hA, S* hB, typename Store<S>::X* chi,
+                   int parity, int first, const long long* __restrict__ tstep, int mchunk) {
+  using R = RT<S>;
+  const long long t = *tstep;
+  for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
+    const BatchTile tl = tiles[q];
+    const BatchInst<S>& I = inst[tl.inst];
+    Phys<R> ph = I.ph;
+    ph.first = first;
+    ph.step = (uint32_t)t;
+    if (I.cosine) {
+      const double c = cos(I.omega * (double)t);
+      ph.Fv[0] = R(I.F0[0] * c);
+      ph.Fv[1] = R(I.F0[1] * c);
+      ph.Fv[2] = R(I.F0[2] * c);
+    }
+    Bufs<S> b;
+    b.f_in = (parity ? fB : fA) + I.f_off;
+    b.f_out = (parity ? fA : fB) + I.f_off;
+    b.h_in = (parity ? hB : hA) + I.h_off;
+    b.h_out = (parity ? hA : hB) + I.h_off;
+    b.chi = chi + I.chi_off;
+    fused_tile<L, S, GX, 1, true, false>(I.g, ph, b, mchunk, tl.bx, 0, tl.bz);
+  }
+}
+
+// t += 1 on the device (one thread), after a batched step
+static __global__ void k_advance_step(long long* t) { *t += 1; }
 
 // ---------------------------------------------------------------------------
 // Split step: velocity field to a device buffer, then collide-and-push with

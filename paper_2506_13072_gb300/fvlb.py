@@ -65,6 +65,12 @@ class fvlb_force(ctypes.Structure):
                 ("k", ctypes.c_double), ("omega", ctypes.c_double)]
 
 
+class fvlb_instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau_s", ctypes.c_double),
+                ("eta_p", ctypes.c_double), ("lam", ctypes.c_double), ("force", fvlb_force),
+                ("walls", ctypes.c_uint)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -101,6 +107,18 @@ _SIGS = {
                              ctypes.c_double, _dp, ctypes.c_void_p, ctypes.c_void_p],
                             ctypes.c_int),
     "fvlb_destroy": ([_H], ctypes.c_int),
+    "fvlb_batch_create": ([ctypes.POINTER(_H), ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(fvlb_instance), ctypes.c_int], ctypes.c_int),
+    "fvlb_batch_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
+    "fvlb_batch_init_fields": ([_H, ctypes.c_int, _dp, _dp, _dp], ctypes.c_int),
+    "fvlb_batch_step": ([_H, ctypes.c_long], ctypes.c_int),
+    "fvlb_batch_fields": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+    "fvlb_batch_info": ([_H, ctypes.POINTER(ctypes.c_longlong), _dp, ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int), _dp], ctypes.c_int),
+    "fvlb_batch_synchronize": ([_H], ctypes.c_int),
+    "fvlb_batch_get_time": ([_H, ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
+    "fvlb_batch_last_error": ([_H], ctypes.c_char_p),
+    "fvlb_batch_destroy": ([_H], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -341,3 +359,87 @@ def compact_to_full(A):
         out[..., a, b] = A[..., k]
         out[..., b, a] = A[..., k]
     return out
+
+
+class Batch:
+    """fvlb_batch_* handle: many D2Q9 problems advanced by one launch per step.
+
+    ``problems`` are workloads.Problem objects (lattice D2Q9)."""
+
+    def __init__(self, problems, precision=FVLB_FP32, stream=None):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        arr = (fvlb_instance * len(problems))()
+        for i, pr in enumerate(problems):
+            a = arr[i]
+            a.nx, a.ny = pr.nx, pr.ny
+            a.tau_s, a.eta_p, a.lam = pr.tau_s, pr.eta_p, pr.lam
+            a.force.kind = int(pr.force_kind)
+            for q in range(3):
+                a.force.F0[q] = float(pr.F0[q]) if q < len(pr.F0) else 0.0
+            a.force.k, a.force.omega = float(pr.k), float(pr.omega)
+            a.walls = int(pr.walls)
+        h = _H()
+        check(lib.fvlb_batch_create(ctypes.byref(h), FVLB_D2Q9, len(problems), arr, int(precision)))
+        self.h = h
+        self.problems = list(problems)
+        if stream is not None:
+            ptr = getattr(stream, "cuda_stream", stream)
+            self._check(lib.fvlb_batch_set_stream(h, ctypes.c_void_p(ptr)))
+
+    def _check(self, code):
+        if code != FVLB_OK:
+            raise FvlbError(code, (lib.fvlb_batch_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fvlb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, index, u=None, p=None, A=None):
+        pr = self.problems[index]
+        N = pr.nx * pr.ny
+        uu = None if u is None else np.ascontiguousarray(np.asarray(u, np.float64).reshape(N * 2))
+        pp = None if p is None else np.ascontiguousarray(np.asarray(p, np.float64).reshape(N))
+        AA = None
+        if A is not None:
+            A = np.asarray(A, np.float64)
+            if A.shape[-2:] == (2, 2):
+                A = full_to_compact(A)
+            AA = np.ascontiguousarray(A.reshape(N * 3))
+        self._check(lib.fvlb_batch_init_fields(self.h, int(index), _ptr(uu), _ptr(pp), _ptr(AA)))
+
+    def step(self, n=1):
+        self._check(lib.fvlb_batch_step(self.h, int(n)))
+
+    def synchronize(self):
+        self._check(lib.fvlb_batch_synchronize(self.h))
+
+    @property
+    def t(self):
+        t = ctypes.c_long()
+        self._check(lib.fvlb_batch_get_time(self.h, ctypes.byref(t)))
+        return t.value
+
+    def fields(self, index, which):
+        pr = self.problems[index]
+        nc = {FVLB_FIELD_U: 2, FVLB_FIELD_P: 1, FVLB_FIELD_A: 3, FVLB_FIELD_TAU_P: 3}[which]
+        out = np.empty(pr.nx * pr.ny * nc, np.float64)
+        self._check(lib.fvlb_batch_fields(self.h, int(index), int(which), _ptr(out), out.size))
+        return out.reshape((pr.ny, pr.nx) if nc == 1 else (pr.ny, pr.nx, nc))
+
+    def info(self):
+        sites = ctypes.c_longlong()
+        bpu = ctypes.c_double()
+        gx, rows = ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_double()
+        self._check(lib.fvlb_batch_info(self.h, ctypes.byref(sites), ctypes.byref(bpu),
+                                        ctypes.byref(gx), ctypes.byref(rows), ctypes.byref(ms)))
+        return dict(sites=sites.value, bytes_per_update=bpu.value, gx=gx.value, rows=rows.value,
+                    tuned_ms_per_step=ms.value)
