@@ -38,6 +38,7 @@ extern "C" {
 #endif
 
 typedef struct fvlb_s *fvlb_t; /* opaque simulation handle */
+typedef struct fvlb_mlp_s *fvlb_mlp_t; /* learned stress closure (see below) */
 
 /* Lattices: D2Q9 (Sec. 2.2 c_i matrix and weights), D3Q19 (Appendix A c_i
  * matrix; weights 1/3, 1/18, 1/36). */
@@ -266,6 +267,59 @@ int fvlb_batch_synchronize(fvlb_batch_t b);
 int fvlb_batch_get_time(fvlb_batch_t b, long *t);
 const char *fvlb_batch_last_error(fvlb_batch_t b);
 int fvlb_batch_destroy(fvlb_batch_t b); /* NULL-safe */
+
+/* ---------------------------------------------------------------------------
+ * Learned stress closure (no counterpart in the paper; a learned stand-in
+ * for the analytic stress source chi of Sec. 2.3).  A network maps a node's
+ * lambda-scaled state x = (lambda d_a u_b [D x D], A - I [C], dt/lambda [2D
+ * only]) to y = lambda chi [C]: D2Q9 8 -> 64 -> 64 -> 3, D3Q19
+ * 15 -> 64 -> 64 -> 6, GELU (tanh form).  It is trained on the GPU (FP32
+ * master weights, Adam) on pairs that the plain method's state provides, and
+ * runs in the step with BF16 weights on the tensor cores (FP32 accumulate);
+ * per node, if ||chi_net - chi|| > tol ||chi|| the analytic chi is used.
+ * ------------------------------------------------------------------------- */
+
+/* Create a network for the lattice with room for `capacity` training pairs;
+ * He-initialised from `seed`. */
+int fvlb_mlp_create(fvlb_mlp_t *out, int lattice, long capacity, unsigned seed);
+
+/* Append the pairs (x, lambda chi) of every stride-th node of the handle's
+ * current state (FP64 or FP32 storage), up to the capacity. */
+int fvlb_mlp_collect(fvlb_mlp_t m, fvlb_t h, long stride);
+int fvlb_mlp_count(fvlb_mlp_t m, long *count);
+/* First n collected pairs to host: x [n][IN], y [n][OUT] (FP32). */
+int fvlb_mlp_get_pairs(fvlb_mlp_t m, float *x, float *y, long n);
+
+/* `steps` Adam steps (beta 0.9 / 0.999) of mean-squared error on minibatches
+ * of `batch` pairs (multiple of 64) drawn with a counter-based hash; the
+ * last minibatch loss is returned.  Repacks the inference weights. */
+int fvlb_mlp_train(fvlb_mlp_t m, long steps, int batch, double lr, double *last_loss);
+
+/* FP32 master parameters W1[64][IN] b1[64] W2[64][64] b2[64] W3[OUT][64]
+ * b3[OUT], concatenated. */
+int fvlb_mlp_num_params(fvlb_mlp_t m, size_t *n);
+int fvlb_mlp_get_params(fvlb_mlp_t m, float *host, size_t count);
+int fvlb_mlp_set_params(fvlb_mlp_t m, const float *host, size_t count);
+
+/* Gradient of the mean-squared error over n host pairs, computed by the
+ * training kernels (FP32), and the loss. */
+int fvlb_mlp_grad(fvlb_mlp_t m, const float *x, const float *y, long n, float *grad,
+                  double *loss);
+
+/* Tensor-core inference (BF16 weights, FP32 accumulate) of n host inputs. */
+int fvlb_mlp_infer(fvlb_mlp_t m, const float *x, long n, float *y);
+
+const char *fvlb_mlp_last_error(fvlb_mlp_t m);
+int fvlb_mlp_destroy(fvlb_mlp_t m); /* NULL-safe */
+
+/* Use the network m (NULL: the analytic source) in the handle's steps, with
+ * fallback tolerance tol; needs FP32 storage and the fused kernel.  The
+ * network must outlive its use.  Resets the closure statistics. */
+int fvlb_set_closure(fvlb_t h, fvlb_mlp_t m, double tol);
+
+/* Node updates that used the network, and fallbacks to the analytic source,
+ * since fvlb_set_closure. */
+int fvlb_closure_stats(fvlb_t h, long long *network_nodes, long long *fallback_nodes);
 
 /* Wait for all GPU work of the handle. */
 int fvlb_synchronize(fvlb_t h);

@@ -66,6 +66,9 @@ struct fvlb_s {
   double* part = nullptr;   // reduction partials
   double* red = nullptr;    // 8 reduced doubles
   double* fbuf = nullptr;   // field output scratch, N * max(D, C) doubles
+  fvlb_mlp_t mlp = nullptr; // learned closure, or null
+  double cl_tol = 1e-2;
+  unsigned long long* cl_count = nullptr;  // [0] network nodes, [1] fallbacks
   fvlb_alloc_fn alloc = nullptr;
   fvlb_free_fn free_ = nullptr;
   void* actx = nullptr;
@@ -113,6 +116,7 @@ void free_all(fvlb_t h) {
   h->f[0] = h->f[1] = h->h[0] = h->h[1] = nullptr;
   h->chi = h->ubuf = h->tables = nullptr;
   h->part = h->red = h->fbuf = nullptr;
+  h->cl_count = nullptr;
   h->allocated = false;
 }
 
@@ -143,6 +147,9 @@ StepDesc make_desc(fvlb_t h) {
   d.step = h->t;
   d.sms = h->sms;
   d.stream = h->stream;
+  d.mlp = h->mlp ? fvlb::mlp_packed(h->mlp) : nullptr;
+  d.cl_tol = h->cl_tol;
+  d.cl_count = h->cl_count;
   double c = 0.0;
   if (h->force.kind == FVLB_FORCE_CONST) c = 1.0;
   if (h->force.kind == FVLB_FORCE_COSINE) c = std::cos(h->force.omega * (double)h->t);
@@ -169,7 +176,10 @@ int allocate(fvlb_t h) {
   const int nparts = fvlb::reduce_parts(h->N);
   h->part = static_cast<double*>(dev_alloc(h, sizeof(double) * 8 * (size_t)nparts));
   h->red = static_cast<double*>(dev_alloc(h, sizeof(double) * 8));
-  bool ok = h->f[0] && h->f[1] && h->h[0] && h->h[1] && h->chi && h->ubuf && h->part && h->red;
+  h->cl_count = static_cast<unsigned long long*>(dev_alloc(h, 2 * sizeof(unsigned long long)));
+  bool ok = h->f[0] && h->f[1] && h->h[0] && h->h[1] && h->chi && h->ubuf && h->part && h->red &&
+            h->cl_count;
+  if (ok && cudaMemset(h->cl_count, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) ok = false;
   if (ok && h->force.kind == FVLB_FORCE_FOUR_ROLL) {
     const int n = 2 * (h->nx + h->ny);
     h->tables = dev_alloc(h, rb * n);
@@ -275,6 +285,16 @@ size_t state_bytes(fvlb_t h) {
 }  // namespace
 
 namespace fvlb {
+
+int state_view(fvlb_t h, StateView* v) {
+  if (!h || !v) return FVLB_EINVAL;
+  int r = ensure_state(h, true);
+  if (r != FVLB_OK) return r;
+  v->lattice = h->lattice;
+  v->N = h->N;
+  v->desc = make_desc(h);
+  return FVLB_OK;
+}
 
 int set_global_error(int code, const char* msg) {
   g_err = msg;
@@ -396,6 +416,8 @@ int fvlb_set_kernel(fvlb_t h, int variant) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (variant != FVLB_KERNEL_FUSED && variant != FVLB_KERNEL_SPLIT)
     return fail(h, FVLB_EINVAL, "fvlb_set_kernel: unknown variant");
+  if (h->mlp && variant != FVLB_KERNEL_FUSED)
+    return fail(h, FVLB_EINVAL, "fvlb_set_kernel: the learned closure needs the fused kernel");
   h->variant = variant;
   return FVLB_OK;
 }
@@ -465,6 +487,41 @@ int fvlb_reduce(fvlb_t h, double out[8]) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_reduce");
   if (out[6] > 0) return fail(h, FVLB_EUNSTABLE, "fvlb_reduce: non-finite values in the state");
+  return FVLB_OK;
+}
+
+int fvlb_set_closure(fvlb_t h, fvlb_mlp_t m, double tol) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  if (m && fvlb::mlp_lattice(m) != h->lattice)
+    return fail(h, FVLB_EINVAL, "fvlb_set_closure: network and grid lattices differ");
+  if (m && h->storage != FVLB_FP32)
+    return fail(h, FVLB_EINVAL, "fvlb_set_closure: the learned closure runs with FP32 storage");
+  if (m && !(tol >= 0.0)) return fail(h, FVLB_EINVAL, "fvlb_set_closure: tol must be >= 0");
+  if (m && h->variant != FVLB_KERNEL_FUSED)
+    return fail(h, FVLB_EINVAL, "fvlb_set_closure: the learned closure needs the fused kernel");
+  int r = ensure_state(h, true);
+  if (r != FVLB_OK) return r;
+  h->mlp = m;
+  h->cl_tol = tol;
+  cudaError_t e = cudaMemsetAsync(h->cl_count, 0, 2 * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_set_closure");
+  return FVLB_OK;
+}
+
+int fvlb_closure_stats(fvlb_t h, long long* network_nodes, long long* fallback_nodes) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  if (!h->allocated) {
+    if (network_nodes) *network_nodes = 0;
+    if (fallback_nodes) *fallback_nodes = 0;
+    return FVLB_OK;
+  }
+  unsigned long long c[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(c, h->cl_count, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_closure_stats");
+  if (network_nodes) *network_nodes = (long long)c[0];
+  if (fallback_nodes) *fallback_nodes = (long long)c[1];
   return FVLB_OK;
 }
 

@@ -31,6 +31,9 @@ struct StepDesc {
   long long step;       // step count t of this launch
   int sms;
   cudaStream_t stream;
+  const void* mlp;      // learned closure: packed weights, or null (analytic chi)
+  double cl_tol;        // fallback tolerance of the learned closure
+  unsigned long long* cl_count;  // [0] nodes on the network, [1] fallbacks
 };
 
 struct InitDesc {
@@ -68,5 +71,16 @@ int set_global_error(int code, const char* msg);
 namespace fvlb {
 // the process-wide allocator hooks (NULL: cudaMalloc / cudaFree)
 void current_allocator(fvlb_alloc_fn* a, fvlb_free_fn* f, void** ctx);
+// the current state of a handle as a launch descriptor (allocating and
+// initialising it to rest if needed)
+struct StateView {
+  int lattice;
+  long long N;
+  StepDesc desc;
+};
+int state_view(fvlb_t h, StateView* v);
+// the packed inference weights of a network (device) and its lattice
+const void* mlp_packed(fvlb_mlp_t m);
+int mlp_lattice(fvlb_mlp_t m);
 
 }  // namespace fvlb

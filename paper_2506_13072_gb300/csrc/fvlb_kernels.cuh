@@ -17,7 +17,10 @@
 // velocity halo suffices.
 #pragma once
 
+#include <type_traits>
+
 #include "fvlb_lattice.cuh"
+#include "fvlb_mlp.cuh"
 
 namespace fvlb {
 
@@ -276,7 +279,21 @@ struct FusedShape {
 // One tile of the fused step: tile (bx, by) of the plane, chunk bz of the
 // march axis.  Called by k_step_fused (one tile per block) and by the
 // batched persistent kernel (many tiles of many grids per block).
-template <class L, class S, int GX, int TY, bool WALLS, bool FW>
+// Shared memory of the learned closure in a tile: the packed network, the
+// BF16 input rows and FP32 output rows of each group's warp, and the chosen
+// chi of every node.
+template <int NG, int C, int NS>
+struct ClosureSmem {
+  MlpPacked P;
+  __nv_bfloat16 X[NG][32][24];
+  float Y[NG][32][8];
+  float chi[C][NS];
+};
+struct NoClosureSmem {
+  int unused;
+};
+
+template <class L, class S, int GX, int TY, bool WALLS, bool FW, bool CL = false>
 __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                                            const Bufs<S>& b, int mchunk, int bx, int by,
                                            int bz) {
@@ -292,6 +309,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   __shared__ R ring[4][D][NE];          // velocity of planes m-1 .. m+2
   __shared__ R sAd[C][NS];              // A - I of the tile nodes
   __shared__ R sPf[C][NS];              // partial sums of f_{i != 0}
+  using CLS = typename std::conditional<CL, ClosureSmem<NG, C, NS>, NoClosureSmem>::type;
+  __shared__ CLS cls;                   // learned closure (CL only)
+  static_assert(!CL || std::is_same<R, float>::value, "the learned closure runs in FP32");
 
   const int nx = g.nx, ny = g.ny;
   const int nm = (D == 3) ? g.nz : g.ny;
@@ -308,6 +328,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const bool filler = warp >= NCW;      // fill warps: ring only
+  if constexpr (CL) mlp_load(cls.P, static_cast<const MlpPacked*>(ph.mlp));
   auto slot = [&](int q) { return (q - m0 + 1) & 3; };
   auto plane_of = [&](int q) -> int {  // -1: beyond a wall
     if (q < 0 || q >= nm) return wall_m ? -1 : (q + nm) % nm;
@@ -368,6 +389,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     __syncthreads();
     for (int m = m0; m < m1; ++m) {
       __syncthreads();               // A: collision loads of plane m done
+      if constexpr (CL) __syncthreads();  // C: learned closure done
       if (m + 2 <= m1) fill(e, m + 2);  // overlaps the collision of plane m
       __syncthreads();               // B
     }
@@ -448,6 +470,89 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     }
     __syncthreads();                    // A
 
+    // ---- learned closure: one warp per group evaluates the network -------------
+    if constexpr (CL) {
+      if (k == 0) {
+        constexpr int IN = MlpDims<D>::IN;
+        float xin[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) xin[q] = 0.f;
+        R gr[D][D], Ad[C], A[C];
+        if (active) {
+#pragma unroll
+          for (int bq = 0; bq < D; ++bq) {
+            const R uo = ring[rc][bq][e_own];
+            {
+              const R up = ring[rc][bq][e_own + 1], um = ring[rc][bq][e_own - 1];
+              R d = R(0.5) * (up - um);
+              if (wall_x && x == 0) d = uo + up * R(1.0 / 3.0);
+              if (wall_x && x == nx - 1) d = -(uo + um * R(1.0 / 3.0));
+              gr[0][bq] = d;
+            }
+            if (D == 3) {
+              const R up = ring[rc][bq][e_own + EX], um = ring[rc][bq][e_own - EX];
+              R d = R(0.5) * (up - um);
+              if (wall_y && y == 0) d = uo + up * R(1.0 / 3.0);
+              if (wall_y && y == ny - 1) d = -(uo + um * R(1.0 / 3.0));
+              gr[1][bq] = d;
+            }
+            {
+              const R up = ring[slot(m + 1)][bq][e_own], um = ring[slot(m - 1)][bq][e_own];
+              R d = R(0.5) * (up - um);
+              if (wall_m && m == 0) d = uo + up * R(1.0 / 3.0);
+              if (wall_m && m == nm - 1) d = -(uo + um * R(1.0 / 3.0));
+              gr[D - 1][bq] = d;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < C; ++q) {
+            Ad[q] = sAd[q][node];
+            A[q] = Ad[q] + (diag<L>(q) ? R(1) : R(0));
+          }
+          int q = 0;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int bq = 0; bq < D; ++bq) xin[q++] = float(ph.lam * gr[a][bq]);
+#pragma unroll
+          for (int c = 0; c < C; ++c) xin[q++] = float(Ad[c]);
+          if (D == 2) xin[q++] = float(ph.inv_lam);
+          (void)IN;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; q += 2)
+          *reinterpret_cast<uint32_t*>(&cls.X[grp][lane][q]) = pack_bf16x2(xin[q], xin[q + 1]);
+        __syncwarp();
+        mlp_warp(cls.P, cls.X[grp], cls.Y[grp]);
+        __syncwarp();
+        bool used = false;
+        if (active) {
+          R chi_an[C];
+          chi_tensor<L, R>(A, Ad, gr, ph.inv_lam, chi_an);
+          float num = 0.f, den = 0.f;
+          float chi_nn[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            chi_nn[c] = cls.Y[grp][lane][c] * float(ph.inv_lam);
+            const float dd = chi_nn[c] - float(chi_an[c]);
+            num += dd * dd;
+            den += float(chi_an[c]) * float(chi_an[c]);
+          }
+          // per-node residual check: fall back to the analytic source
+          used = num <= ph.cl_tol2 * den;
+#pragma unroll
+          for (int c = 0; c < C; ++c) cls.chi[c][node] = used ? chi_nn[c] : float(chi_an[c]);
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, active);
+        const unsigned use = __ballot_sync(0xffffffffu, used);
+        if (lane == 0 && ph.cl_count && act) {
+          atomicAdd(ph.cl_count, (unsigned long long)__popc(use));
+          atomicAdd(ph.cl_count + 1, (unsigned long long)__popc(act & ~use));
+        }
+      }
+      __syncthreads();                  // C
+    }
+
     // ---- collision phase ------------------------------------------------------
     if (active) {
       R u[D];
@@ -481,6 +586,12 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 #pragma unroll
       for (int q = 0; q < C; ++q) {
         if (q != k) continue;
+        if constexpr (CL) {
+          chi_k = cls.chi[q][node];
+          Ad_k = Ad[q];
+          A_k = Ad[q] + (diag<L>(q) ? R(1) : R(0));
+          continue;
+        }
         const int a = L::ca(q), bb = L::cb(q);
         R v = -Ad[q] * ph.inv_lam;
 #pragma unroll
@@ -606,10 +717,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   }
 }
 
-template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW>
+template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL = false>
 __global__ void __launch_bounds__(FusedShape<L, GX, TY, FW>::NT, MINB)
     k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
-  fused_tile<L, S, GX, TY, WALLS, FW>(g, ph, b, mchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+  fused_tile<L, S, GX, TY, WALLS, FW, CL>(g, ph, b, mchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------

@@ -259,6 +259,10 @@ struct Phys {
   const R* cys;       // cos(k y)
   int first;          // first step: chi of the previous step := chi
   uint32_t step;      // step counter (stochastic-rounding stream)
+  R lam;              // lambda
+  const void* mlp;    // learned closure: packed network weights (or null)
+  float cl_tol2;      // squared fallback tolerance of the learned closure
+  unsigned long long* cl_count;  // [0] nodes on the network, [1] fallbacks
 };
 
 template <class S>

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "fvlb_internal.h"
 #include "fvlb_kernels.cuh"
@@ -44,6 +45,10 @@ Phys<R> make_phys(const StepDesc& d) {
   p.cys = t ? t + 2 * d.nx + d.ny : nullptr;
   p.first = d.first;
   p.step = (uint32_t)d.step;
+  p.lam = R(d.lambda);
+  p.mlp = d.mlp;
+  p.cl_tol2 = float(d.cl_tol * d.cl_tol);
+  p.cl_count = d.cl_count;
   return p;
 }
 
@@ -71,6 +76,15 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
   constexpr int NT = FusedShape<L, GX, TY, FW>::NT;
+  if constexpr (std::is_same<S, float>::value) {
+    if (d.mlp) {  // learned closure (FP32 storage only); one block per SM
+      if (d.walls)
+        k_step_fused<L, S, GX, TY, 1, true, FW, true><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
+      else
+        k_step_fused<L, S, GX, TY, 1, false, FW, true><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
+      return cudaGetLastError();
+    }
+  }
   if (d.walls)
     k_step_fused<L, S, GX, TY, MINB, true, FW><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
   else

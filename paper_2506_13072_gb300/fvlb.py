@@ -82,6 +82,7 @@ lib = ctypes.CDLL(LIB_PATH)
 
 _H = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _SIGS = {
     "fvlb_set_allocator": ([ALLOC_FN, FREE_FN, ctypes.c_void_p], ctypes.c_int),
     "fvlb_create": ([ctypes.POINTER(_H), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -119,6 +120,21 @@ _SIGS = {
     "fvlb_batch_get_time": ([_H, ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
     "fvlb_batch_last_error": ([_H], ctypes.c_char_p),
     "fvlb_batch_destroy": ([_H], ctypes.c_int),
+    "fvlb_mlp_create": ([ctypes.POINTER(_H), ctypes.c_int, ctypes.c_long, ctypes.c_uint], ctypes.c_int),
+    "fvlb_mlp_collect": ([_H, _H, ctypes.c_long], ctypes.c_int),
+    "fvlb_mlp_count": ([_H, ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
+    "fvlb_mlp_get_pairs": ([_H, _fp, _fp, ctypes.c_long], ctypes.c_int),
+    "fvlb_mlp_train": ([_H, ctypes.c_long, ctypes.c_int, ctypes.c_double, _dp], ctypes.c_int),
+    "fvlb_mlp_num_params": ([_H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "fvlb_mlp_get_params": ([_H, _fp, ctypes.c_size_t], ctypes.c_int),
+    "fvlb_mlp_set_params": ([_H, _fp, ctypes.c_size_t], ctypes.c_int),
+    "fvlb_mlp_grad": ([_H, _fp, _fp, ctypes.c_long, _fp, _dp], ctypes.c_int),
+    "fvlb_mlp_infer": ([_H, _fp, ctypes.c_long, _fp], ctypes.c_int),
+    "fvlb_mlp_last_error": ([_H], ctypes.c_char_p),
+    "fvlb_mlp_destroy": ([_H], ctypes.c_int),
+    "fvlb_set_closure": ([_H, _H, ctypes.c_double], ctypes.c_int),
+    "fvlb_closure_stats": ([_H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+                           ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -336,6 +352,16 @@ class Simulation:
         check(lib.fvlb_bytes_per_update(self.h, ctypes.byref(b)), self.h)
         return b.value
 
+    def set_closure(self, mlp, tol=1e-2):
+        """Use a trained Mlp for the stress source (None: analytic)."""
+        self._mlp = mlp
+        check(lib.fvlb_set_closure(self.h, mlp.h if mlp is not None else None, float(tol)), self.h)
+
+    def closure_stats(self):
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        check(lib.fvlb_closure_stats(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
+        return dict(network=a.value, fallback=b.value)
+
 
 def full_to_compact(A):
     """[..., D, D] -> [..., C] in the library's compact order."""
@@ -443,3 +469,99 @@ class Batch:
                                         ctypes.byref(gx), ctypes.byref(rows), ctypes.byref(ms)))
         return dict(sites=sites.value, bytes_per_update=bpu.value, gx=gx.value, rows=rows.value,
                     tuned_ms_per_step=ms.value)
+
+
+def _f32p(a):
+    return a.ctypes.data_as(_fp)
+
+
+class Mlp:
+    """fvlb_mlp_* handle: the learned stress closure's network."""
+
+    def __init__(self, lattice, capacity=1 << 20, seed=0):
+        h = _H()
+        check(lib.fvlb_mlp_create(ctypes.byref(h), int(lattice), int(capacity), int(seed)))
+        self.h = h
+        self.lattice = lattice
+        self.IN, self.OUT = (8, 3) if lattice == FVLB_D2Q9 else (15, 6)
+
+    def _check(self, code):
+        if code != FVLB_OK:
+            raise FvlbError(code, (lib.fvlb_mlp_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fvlb_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def collect(self, sim, stride=1):
+        self._check(lib.fvlb_mlp_collect(self.h, sim.h, int(stride)))
+
+    @property
+    def count(self):
+        n = ctypes.c_long()
+        self._check(lib.fvlb_mlp_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def pairs(self, n=None):
+        n = self.count if n is None else n
+        x = np.empty((n, self.IN), np.float32)
+        y = np.empty((n, self.OUT), np.float32)
+        self._check(lib.fvlb_mlp_get_pairs(self.h, _f32p(x), _f32p(y), n))
+        return x, y
+
+    def train(self, steps, batch=1024, lr=1e-3):
+        loss = ctypes.c_double()
+        self._check(lib.fvlb_mlp_train(self.h, int(steps), int(batch), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def params(self):
+        n = ctypes.c_size_t()
+        self._check(lib.fvlb_mlp_num_params(self.h, ctypes.byref(n)))
+        out = np.empty(n.value, np.float32)
+        self._check(lib.fvlb_mlp_get_params(self.h, _f32p(out), out.size))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        self._check(lib.fvlb_mlp_set_params(self.h, _f32p(flat), flat.size))
+
+    def grad(self, x, y):
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        n = ctypes.c_size_t()
+        self._check(lib.fvlb_mlp_num_params(self.h, ctypes.byref(n)))
+        g = np.empty(n.value, np.float32)
+        loss = ctypes.c_double()
+        self._check(lib.fvlb_mlp_grad(self.h, _f32p(x), _f32p(y), x.shape[0], _f32p(g),
+                                      ctypes.byref(loss)))
+        return loss.value, g
+
+    def infer(self, x):
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.empty((x.shape[0], self.OUT), np.float32)
+        self._check(lib.fvlb_mlp_infer(self.h, _f32p(x), x.shape[0], _f32p(y)))
+        return y
+
+
+def mlp_flatten(p):
+    """oracle-style parameter dict -> the library's flat FP32 order."""
+    return np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(),
+                           p["b3"]]).astype(np.float32)
+
+
+def mlp_unflatten(flat, nin, nout, H=64):
+    sizes = [("W1", (H, nin)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (nout, H)),
+             ("b3", (nout,))]
+    out, o = {}, 0
+    for name, shp in sizes:
+        n = int(np.prod(shp))
+        out[name] = np.asarray(flat[o:o + n], np.float64).reshape(shp)
+        o += n
+    return out
