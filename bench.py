@@ -275,6 +275,46 @@ def batch_rate(F, precision, stream, steps=40):
             "launches_per_step": 1}
 
 
+def closure_rate(F, stream, steps=10):
+    """D3Q19 Taylor-Green 256^3 FP32 with the learned closure: the network is
+    trained on pairs from Taylor-Green 32^3 runs of the plain method (Wi 1 and
+    0.2; relative loss), then replaces chi where its per-node residual is
+    within 1e-2."""
+    import torch
+
+    from paper_2506_13072_gb300 import workloads as W
+
+    net = F.Mlp(F.FVLB_D3Q19, capacity=1 << 20, seed=0)
+    for Wi in (1.0, 0.2):
+        small = W.taylor_green_3d(n=32, U0=0.02, Re=100, Wi=Wi, beta=0.5)
+        s = F.Simulation.from_problem(small, precision=F.FVLB_FP32)
+        s.init_fields(small.u0, small.p0, small.A0)
+        for _ in range(8):
+            s.step(100)
+            net.collect(s, stride=5)
+        s.close()
+    net.set_loss(1e-3)
+    for n, b, lr in ((10000, 1024, 2e-3), (10000, 2048, 5e-4), (10000, 4096, 1e-4)):
+        net.train(n, batch=b, lr=lr)
+    pr = tgv_problem(WORKLOAD["n"])
+    sim = F.Simulation.from_problem(pr, precision=F.FVLB_FP32, stream=stream)
+    sim.init_fields(pr.u0, pr.p0, pr.A0)
+    sim.set_closure(net, tol=1e-2)
+    sim.step(3)
+    torch.cuda.synchronize()
+    dt = time_steps(sim, steps, stream)
+    st = sim.closure_stats()
+    bpu = sim.bytes_per_update()
+    sim.close()
+    net.close()
+    tot = st["network"] + st["fallback"]
+    return {"mlups": round(pr.sites * steps / dt / 1e6, 1),
+            "gbs_algorithmic": round(bpu * pr.sites * steps / dt / 1e9, 1),
+            "bytes_per_update": bpu, "ms_per_step": round(1e3 * dt / steps, 4),
+            "network_share_of_node_updates": round(st["network"] / max(1, tot), 4),
+            "tol": 1e-2}
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -352,6 +392,8 @@ def run_ours(args, rank, world, dist):
         for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("fp32", F.FVLB_FP32)):
             forms[f"batched_512_d2q9_{name}"] = batch_rate(F, prec, stream)
             torch.cuda.empty_cache()
+        forms["d3q19_256^3_fp32_learned_closure"] = closure_rate(F, stream)
+        torch.cuda.empty_cache()
         for k, v in forms.items():
             v["frac_of_hbm_peak"] = round(v["gbs_algorithmic"] / peak, 3)
         torch.cuda.synchronize()

@@ -290,7 +290,12 @@ int fvlb_mlp_count(fvlb_mlp_t m, long *count);
 /* First n collected pairs to host: x [n][IN], y [n][OUT] (FP32). */
 int fvlb_mlp_get_pairs(fvlb_mlp_t m, float *x, float *y, long n);
 
-/* `steps` Adam steps (beta 0.9 / 0.999) of mean-squared error on minibatches
+/* Loss of training and of fvlb_mlp_grad: delta = 0 (default) the mean
+ * squared error; delta > 0 the error of each pair weighted by
+ * 1 / (mean_o y_o^2 + delta^2), i.e. relative to the pair's target. */
+int fvlb_mlp_set_loss(fvlb_mlp_t m, double delta);
+
+/* `steps` Adam steps (beta 0.9 / 0.999) of the loss on minibatches
  * of `batch` pairs (multiple of 64) drawn with a counter-based hash; the
  * last minibatch loss is returned.  Repacks the inference weights. */
 int fvlb_mlp_train(fvlb_mlp_t m, long steps, int batch, double lr, double *last_loss);
@@ -301,8 +306,8 @@ int fvlb_mlp_num_params(fvlb_mlp_t m, size_t *n);
 int fvlb_mlp_get_params(fvlb_mlp_t m, float *host, size_t count);
 int fvlb_mlp_set_params(fvlb_mlp_t m, const float *host, size_t count);
 
-/* Gradient of the mean-squared error over n host pairs, computed by the
- * training kernels (FP32), and the loss. */
+/* Gradient of the loss over n host pairs, computed by the training kernels
+ * (FP32), and the loss. */
 int fvlb_mlp_grad(fvlb_mlp_t m, const float *x, const float *y, long n, float *grad,
                   double *loss);
 

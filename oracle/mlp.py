@@ -56,13 +56,16 @@ def forward(p, x):
     return y, (x, z1, h1, z2, h2)
 
 
-def loss_and_grad(p, x, t):
-    """Mean squared error over all outputs and its gradient."""
+def loss_and_grad(p, x, t, delta=0.0):
+    """Mean squared error over all outputs and its gradient.  With delta > 0
+    each sample's error is weighted by 1 / (mean_o t_o^2 + delta^2), a
+    relative error with a floor."""
     y, (x, z1, h1, z2, h2) = forward(p, x)
     n, nout = y.shape
     r = y - t
-    loss = float((r * r).mean())
-    dy = 2.0 * r / (n * nout)
+    w = np.ones((n, 1)) if delta <= 0 else 1.0 / ((t * t).mean(axis=1, keepdims=True) + delta * delta)
+    loss = float((w * r * r).mean())
+    dy = 2.0 * w * r / (n * nout)
     g = {}
     g["W3"] = dy.T @ h2
     g["b3"] = dy.sum(axis=0)

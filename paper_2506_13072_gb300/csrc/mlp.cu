@@ -117,7 +117,8 @@ template <int IN, int OUT>
 __global__ void __launch_bounds__(kTB)
     k_mlp_grad(const float* __restrict__ prm, const float* __restrict__ X,
                const float* __restrict__ T, long long count, long long n, int sample_seed,
-               long long batch_base, float* __restrict__ part, float* __restrict__ part_loss) {
+               long long batch_base, float delta2, float* __restrict__ part,
+               float* __restrict__ part_loss) {
   using PP = MlpParams<IN, OUT>;
   constexpr int H = kMlpH;
   extern __shared__ float sm[];
@@ -156,12 +157,19 @@ __global__ void __launch_bounds__(kTB)
     z2[tid * LD + j] = a;
     h2[tid * LD + j] = gelu_acc(a, nullptr);
   }
-  const float scale = 2.0f / (float(n) * float(OUT));
+  // sample weight: 1, or 1 / (mean_o t_o^2 + delta^2) for the relative loss
+  float wgt = 1.f;
+  if (delta2 > 0.f && valid) {
+    float tt = 0.f;
+    for (int o = 0; o < OUT; ++o) tt += T[src * OUT + o] * T[src * OUT + o];
+    wgt = 1.f / (tt / float(OUT) + delta2);
+  }
+  const float scale = 2.0f * wgt / (float(n) * float(OUT));
   for (int o = 0; o < OUT; ++o) {
     float y = W[PP::B3 + o];
     for (int k = 0; k < H; ++k) y += W[PP::W3 + o * H + k] * h2[tid * LD + k];
     const float r = valid ? y - T[src * OUT + o] : 0.f;
-    loss += r * r;
+    loss += wgt * r * r;
     dy[tid * OUT + o] = scale * r;
   }
   // backward through layer 3 and GELU: dz2 (stored over z2)
@@ -309,6 +317,7 @@ struct fvlb_mlp_s {
   double* loss = nullptr;
   MlpPacked* packed = nullptr;
   long long adam_t = 0;
+  double delta = 0.0;       // relative-loss floor (0: plain mean squared error)
   cudaStream_t stream = nullptr;
   fvlb_alloc_fn alloc = nullptr;
   fvlb_free_fn free_ = nullptr;
@@ -343,14 +352,15 @@ size_t train_smem(int IN, int OUT, int NP) {
 
 cudaError_t launch_grad(fvlb_mlp_t m, const float* X, const float* T, long long count,
                         long long n, int seed, long long base, int nblocks) {
+  const float d2 = float(m->delta * m->delta);
   const size_t sm = train_smem(m->IN, m->OUT, m->NP);
   if (m->D == 2) {
     cudaFuncSetAttribute(k_mlp_grad<8, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_mlp_grad<8, 3><<<nblocks, kTB, sm, m->stream>>>(m->prm, X, T, count, n, seed, base, m->part,
-                                                      m->part_loss);
+    k_mlp_grad<8, 3><<<nblocks, kTB, sm, m->stream>>>(m->prm, X, T, count, n, seed, base, d2,
+                                                      m->part, m->part_loss);
   } else {
     cudaFuncSetAttribute(k_mlp_grad<15, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_mlp_grad<15, 6><<<nblocks, kTB, sm, m->stream>>>(m->prm, X, T, count, n, seed, base,
+    k_mlp_grad<15, 6><<<nblocks, kTB, sm, m->stream>>>(m->prm, X, T, count, n, seed, base, d2,
                                                        m->part, m->part_loss);
   }
   return cudaGetLastError();
@@ -502,6 +512,13 @@ int fvlb_mlp_collect(fvlb_mlp_t m, fvlb_t h, long stride) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
   if (e != cudaSuccess) return mfail(m, FVLB_ECUDA, std::string("fvlb_mlp_collect: ") + cudaGetErrorString(e));
   m->count += n;
+  return FVLB_OK;
+}
+
+int fvlb_mlp_set_loss(fvlb_mlp_t m, double delta) {
+  if (!m) return set_global_error(FVLB_EINVAL, "NULL mlp");
+  if (!(delta >= 0.0) || !std::isfinite(delta)) return mfail(m, FVLB_EINVAL, "fvlb_mlp_set_loss: delta must be >= 0");
+  m->delta = delta;
   return FVLB_OK;
 }
 

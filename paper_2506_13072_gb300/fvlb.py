@@ -123,6 +123,7 @@ _SIGS = {
     "fvlb_mlp_create": ([ctypes.POINTER(_H), ctypes.c_int, ctypes.c_long, ctypes.c_uint], ctypes.c_int),
     "fvlb_mlp_collect": ([_H, _H, ctypes.c_long], ctypes.c_int),
     "fvlb_mlp_count": ([_H, ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
+    "fvlb_mlp_set_loss": ([_H, ctypes.c_double], ctypes.c_int),
     "fvlb_mlp_get_pairs": ([_H, _fp, _fp, ctypes.c_long], ctypes.c_int),
     "fvlb_mlp_train": ([_H, ctypes.c_long, ctypes.c_int, ctypes.c_double, _dp], ctypes.c_int),
     "fvlb_mlp_num_params": ([_H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -515,6 +516,10 @@ class Mlp:
         y = np.empty((n, self.OUT), np.float32)
         self._check(lib.fvlb_mlp_get_pairs(self.h, _f32p(x), _f32p(y), n))
         return x, y
+
+    def set_loss(self, delta=0.0):
+        """delta > 0: relative loss, each pair weighted 1/(mean t^2 + delta^2)."""
+        self._check(lib.fvlb_mlp_set_loss(self.h, float(delta)))
 
     def train(self, steps, batch=1024, lr=1e-3):
         loss = ctypes.c_double()

@@ -52,8 +52,8 @@ def test_tensor_core_inference(lattice):
     net.close()
 
 
-@pytest.mark.parametrize("lattice", [9, 19])
-def test_training_gradient(lattice):
+@pytest.mark.parametrize("lattice,delta", [(9, 0.0), (19, 0.0), (9, 0.05)])
+def test_training_gradient(lattice, delta):
     F = fvlb()
     nin, nout = M.dims(lattice)
     p = M.init_params(lattice, seed=7)
@@ -62,11 +62,12 @@ def test_training_gradient(lattice):
         p[k] = rng.normal(scale=0.1, size=p[k].shape)
     net = F.Mlp(lattice, capacity=16)
     net.set_params(F.mlp_flatten(p))
+    net.set_loss(delta)
     p32 = F.mlp_unflatten(net.params(), nin, nout)
     x = rng.normal(size=(200, nin)).astype(np.float32)
     t = rng.normal(size=(200, nout)).astype(np.float32)
     loss, g = net.grad(x, t)
-    lref, gref = M.loss_and_grad(p32, x.astype(np.float64), t.astype(np.float64))
+    lref, gref = M.loss_and_grad(p32, x.astype(np.float64), t.astype(np.float64), delta)
     assert loss == pytest.approx(lref, rel=1e-5)
     gg = F.mlp_unflatten(g, nin, nout)
     for k in gref:
@@ -122,8 +123,9 @@ def _train_2d(F, seed=0):
             s.step(500)
             net.collect(s, stride=3)
         s.close()
-    loss = net.train(3000, batch=1024, lr=2e-3)
-    loss = net.train(2000, batch=2048, lr=3e-4)
+    net.set_loss(1e-3)   # relative error per pair (floor 1e-3)
+    for steps, batch, lr in ((10000, 1024, 2e-3), (10000, 2048, 5e-4), (10000, 4096, 1e-4)):
+        loss = net.train(steps, batch=batch, lr=lr)
     return net, loss
 
 
@@ -136,9 +138,7 @@ def test_learned_closure_in_the_step():
     throughput ratio against the analytic step."""
     F = fvlb()
     net, loss = _train_2d(F)
-    x, y = net.pairs()
-    scale = float((y.astype(np.float64) ** 2).mean())
-    assert loss < 1e-2 * scale, (loss, scale)
+    assert loss < 3e-2, loss          # relative mean squared error of the last minibatch
     pr = W.four_roll(n=64, Wi=0.5, beta=0.5)
     s = gpu_sim(pr, F.FVLB_FP32)
     s.set_closure(net, tol=1e-2)
@@ -151,6 +151,7 @@ def test_learned_closure_in_the_step():
     et = rel_l2(s.tau_p(), compact(o.tau_p()), tfloor)
     served = st["network"] / max(1, st["network"] + st["fallback"])
     assert st["network"] + st["fallback"] == 1000 * pr.sites
+    assert served > 0.3, served
     assert eu < 1e-3 and et < 1e-3, (eu, et, served)
     # throughput with and without the network on a larger grid
     big = W.four_roll(n=1024, Wi=0.5, beta=0.5)

@@ -7,8 +7,8 @@ import pytest
 from oracle import mlp
 
 
-@pytest.mark.parametrize("lattice", [9, 19])
-def test_gradient_matches_finite_differences(lattice):
+@pytest.mark.parametrize("lattice,delta", [(9, 0.0), (19, 0.0), (9, 0.1)])
+def test_gradient_matches_finite_differences(lattice, delta):
     nin, nout = mlp.dims(lattice)
     rng = np.random.default_rng(1)
     p = mlp.init_params(lattice, seed=2)
@@ -16,7 +16,7 @@ def test_gradient_matches_finite_differences(lattice):
         p[k] = rng.normal(scale=0.1, size=p[k].shape)
     x = rng.normal(size=(7, nin))
     t = rng.normal(size=(7, nout))
-    _, g = mlp.loss_and_grad(p, x, t)
+    _, g = mlp.loss_and_grad(p, x, t, delta)
     eps = 1e-6
     for name, arr in p.items():
         flat = arr.reshape(-1)
@@ -24,9 +24,9 @@ def test_gradient_matches_finite_differences(lattice):
         for j in idx:
             old = flat[j]
             flat[j] = old + eps
-            lp, _ = mlp.loss_and_grad(p, x, t)
+            lp, _ = mlp.loss_and_grad(p, x, t, delta)
             flat[j] = old - eps
-            lm, _ = mlp.loss_and_grad(p, x, t)
+            lm, _ = mlp.loss_and_grad(p, x, t, delta)
             flat[j] = old
             fd = (lp - lm) / (2 * eps)
             assert g[name].reshape(-1)[j] == pytest.approx(fd, rel=1e-6, abs=1e-10), (name, j)
