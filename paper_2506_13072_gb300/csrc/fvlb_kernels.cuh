@@ -27,6 +27,21 @@ namespace fvlb {
 template <class S>
 using RT = typename Store<S>::R;
 
+// Asynchronous global -> shared copies (cp.async, one element per thread);
+// the copies of a thread become visible to it after cp_wait_all.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Make a pointer opaque to the compiler at this point of the program.  Used
 // to stop the 114 population addresses of a D3Q19 site from being computed
 // once and kept live (in registers) between the two reads of the stress
@@ -311,6 +326,15 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   __shared__ R sPf[C][NS];              // partial sums of f_{i != 0}
   using CLS = typename std::conditional<CL, ClosureSmem<NG, C, NS>, NoClosureSmem>::type;
   __shared__ CLS cls;                   // learned closure (CL only)
+  // Prefetch of the next plane's populations of each collision thread
+  // (Q stress populations, its flow populations and chi) with cp.async,
+  // double-buffered; FP32 storage (4-byte copies; the stage then fits the
+  // 48 KB of static shared memory), not with the learned closure.
+  constexpr bool PF = sizeof(S) == 4 && !CL;
+  constexpr int NPF = Q + NFM + 1;
+  constexpr int NCT = NCW * 32;
+  using Stage = typename std::conditional<PF, S[2][NPF][NCT], int>::type;
+  __shared__ Stage stage;
   static_assert(!CL || std::is_same<R, float>::value, "the learned closure runs in FP32");
 
   const int nx = g.nx, ny = g.ny;
@@ -366,10 +390,16 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 #pragma unroll
     for (int a = 0; a < D; ++a) ring[r][a][e] = u[a];
   };
+  // this thread's ring slot (fixed for the whole tile): node coordinates
+  // computed once, outside the march
+  // (fill warps only; the in-collision fill recomputes it per plane, which
+  // measured faster there than holding it in registers)
+  int sgx = 0, sgy = 0;
+  const bool shas = FW && filler && slot_node(tid - NCW * 32, sgx, sgy);
   auto fill = [&](int e, int q) {
     if (e >= NE) return;
-    int gx = 0, gy = 0;
-    const bool has = slot_node(e, gx, gy);
+    int gx = sgx, gy = sgy;
+    const bool has = FW ? shas : slot_node(e, gx, gy);
     const int mm = plane_of(q);
     const bool ok = has && mm >= 0;
     R fv[Q];
@@ -421,6 +451,26 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   const int ox_m = (x == 0) ? (nx - 1) : -1;
   const int oy_p = (D == 3) ? ((y == ny - 1) ? -(ny - 1) * nx : nx) : 0;
   const int oy_m = (D == 3) ? ((y == 0) ? (ny - 1) * nx : -nx) : 0;
+  // issue the copies of plane q's populations into stage buffer q & 1
+  auto prefetch = [&](int q) {
+    if constexpr (PF) {
+      if (!active || q >= m1) return;
+      const long long sq = (D == 3) ? ((long long)q * ny + y) * nx + x : (long long)q * nx + x;
+      const uint32_t sq32 = (uint32_t)sq;
+      const int st = q & 1;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) cp_async<sizeof(S)>(&stage[st][i][tid], hin_k + ((uint32_t)i * P32 + sq32));
+#pragma unroll
+      for (int j = 0; j < NFM; ++j) {
+        const int i = k + j * C;
+        if (i < Q) cp_async<sizeof(S)>(&stage[st][Q + j][tid], b.f_in + ((uint32_t)i * P32 + sq32));
+      }
+      if (sizeof(X) == sizeof(S))
+        cp_async<sizeof(S)>(&stage[st][Q + NFM][tid], b.chi + ((uint32_t)k * P32 + sq32));
+      cp_commit();
+    }
+  };
+  prefetch(m0);
   __syncthreads();                      // ring prologue
 
   for (int m = m0; m < m1; ++m) {
@@ -445,14 +495,26 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     R hv[Q], fo[NFM];
     R old = R(0);
     if (active) {
+      if constexpr (PF) {
+        // this plane's copies (issued one plane ago); then start the next
+        cp_wait_all();
+        const int st = m & 1;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) hv[i] = Store<S>::ld(hin_k + ((uint32_t)i * P32 + s32));
+        for (int i = 0; i < Q; ++i) hv[i] = R(stage[st][i][tid]);
 #pragma unroll
-      for (int j = 0; j < NFM; ++j) {
-        const int i = k + j * C;
-        fo[j] = i < Q ? Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s32)) : R(0);
+        for (int j = 0; j < NFM; ++j) fo[j] = (k + j * C < Q) ? R(stage[st][Q + j][tid]) : R(0);
+        old = sizeof(X) == sizeof(S) ? R(stage[st][Q + NFM][tid]) : R(b.chi[(uint32_t)k * P32 + s32]);
+        prefetch(m + 1);
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) hv[i] = Store<S>::ld(hin_k + ((uint32_t)i * P32 + s32));
+#pragma unroll
+        for (int j = 0; j < NFM; ++j) {
+          const int i = k + j * C;
+          fo[j] = i < Q ? Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s32)) : R(0);
+        }
+        old = R(b.chi[(uint32_t)k * P32 + s32]);
       }
-      old = R(b.chi[(uint32_t)k * P32 + s32]);
       R a = R(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) a += hv[i];
