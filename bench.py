@@ -218,6 +218,21 @@ def config_dict(args=None, note=""):
 # GPU
 # ---------------------------------------------------------------------------
 
+def aggregate(dt_local, units_local, dist):
+    """Whole-job rate of weakly scaled replicas: the units of all ranks over
+    the slowest rank's time (max over ranks).  Returns (dt_max, units_total)."""
+    if dist is None:
+        return dt_local, units_local
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([dt_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def time_steps(sim, steps, stream):
     import torch
 
@@ -339,17 +354,15 @@ def run_ours(args, rank, world, dist):
     with ClockSampler(local) as clk:
         dt = time_steps(sim, args.steps, stream)
     torch.cuda.synchronize()
+    dt, units = aggregate(dt, pr.sites * args.steps, dist)
     if dist is not None:
-        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
         dist.barrier()
     diag = sim.reduce(check_finite=False)
     bpu = sim.bytes_per_update()
     sim.close()
 
     sites = pr.sites
-    value = sites * args.steps * world / dt / 1e6
+    value = units / dt / 1e6
     launch_s = dt / args.steps                 # one fused launch per step
     achieved = bpu * sites / launch_s / 1e9    # GB/s, algorithmic bytes
     peaks, which = measured_peaks()

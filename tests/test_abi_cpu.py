@@ -2,6 +2,7 @@
 every entry point declared in include/fvlb.h, and validates arguments before
 touching CUDA."""
 import ctypes
+import os
 
 import pytest
 
@@ -65,3 +66,21 @@ def test_compact_full_roundtrip():
         A = rng.normal(size=(4, D, D))
         A = A + np.swapaxes(A, -1, -2)
         assert np.array_equal(F.compact_to_full(F.full_to_compact(A)), A)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: importing the binding without the built CUDA library
+    raises ImportError."""
+    import shutil
+    import subprocess
+    import sys
+
+    pkg = tmp_path / "paper_2506_13072_gb300"
+    pkg.mkdir()
+    src = os.path.join(os.path.dirname(F.__file__), "fvlb.py")
+    shutil.copy(src, pkg / "fvlb.py")
+    (pkg / "__init__.py").write_text("")
+    code = "import paper_2506_13072_gb300.fvlb"
+    r = subprocess.run([sys.executable, "-c", code], cwd=tmp_path, capture_output=True, text=True)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "not built" in r.stderr

@@ -281,3 +281,23 @@ def test_nonfinite_is_reported():
         s.reduce()
     assert e.value.code == F.FVLB_EUNSTABLE
     s.close()
+
+
+def test_allocation_failure_is_reported():
+    """A device allocator that fails (injected through the allocator hooks)
+    surfaces as FVLB_ENOMEM, and the handle stays usable for destruction."""
+    import ctypes
+
+    F = fvlb()
+    fail_alloc = F.ALLOC_FN(lambda n, ctx: None)
+    noop_free = F.FREE_FN(lambda p, ctx: None)
+    assert F.lib.fvlb_set_allocator(fail_alloc, noop_free, None) == F.FVLB_OK
+    try:
+        s = F.Simulation(F.FVLB_D2Q9, 16, 16, 1, 0.8, 0.1, 10.0)
+        with pytest.raises(F.FvlbError) as e:
+            s.step(1)
+        assert e.value.code == F.FVLB_ENOMEM
+        s.close()
+    finally:
+        F._alloc_refs = None
+        F.use_torch_allocator()
