@@ -321,11 +321,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   constexpr int NFM = Split<L>::NFMAX;
   static_assert(D == 3 || TY == 1, "2D tiles are one row high");
   static_assert(FW || NE <= NCW * 32, "in-collision fill: one ring slot per thread");
-  __shared__ R ring[4][D][NE];          // velocity of planes m-1 .. m+2
-  __shared__ R sAd[C][NS];              // A - I of the tile nodes
-  __shared__ R sPf[C][NS];              // partial sums of f_{i != 0}
   using CLS = typename std::conditional<CL, ClosureSmem<NG, C, NS>, NoClosureSmem>::type;
-  __shared__ CLS cls;                   // learned closure (CL only)
   // Prefetch of the next plane's populations of each collision thread
   // (Q stress populations, its flow populations and chi) with cp.async,
   // double-buffered; FP32 storage (4-byte copies; the stage then fits the
@@ -334,6 +330,16 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   constexpr int NPF = Q + NFM + 1;
   constexpr int NCT = NCW * 32;
   using Stage = typename std::conditional<PF, S[2][NPF][NCT], int>::type;
+  // The exchange arrays sAd / sPf are double-buffered by plane parity when
+  // static shared memory allows: plane m + 1 then writes the other copy
+  // while slower warps still read plane m's, and one barrier per plane
+  // suffices (otherwise a second barrier closes each plane).
+  constexpr size_t kSmemOne = sizeof(R) * 4 * D * NE + sizeof(CLS) + sizeof(Stage);
+  constexpr int NBUF = (kSmemOne + 2 * 2 * sizeof(R) * C * NS <= 48 * 1024) ? 2 : 1;
+  __shared__ R ring[4][D][NE];          // velocity of planes m-1 .. m+2
+  __shared__ R sAd[NBUF][C][NS];        // A - I of the tile nodes
+  __shared__ R sPf[NBUF][C][NS];        // partial sums of f_{i != 0}
+  __shared__ CLS cls;                   // learned closure (CL only)
   __shared__ Stage stage;
   static_assert(!CL || std::is_same<R, float>::value, "the learned closure runs in FP32");
 
@@ -410,6 +416,12 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     fill_store(e, ok, mm, gx, gy, fv, q);
   };
 
+  // Ring slot of plane q: (q - m0 + 1) mod 4.  The collision of plane m
+  // (between barriers A(m) and A(m + 1)) reads the slots of m - 1, m and
+  // m + 1.  In the same interval the fill warps write plane m + 2, and the
+  // in-collision fill (memory phase of m + 1) writes plane m + 2 as well:
+  // its slot (that of plane m - 2) was last read by the collision of plane
+  // m - 1, which every warp finished before A(m).
   if (FW && filler) {
     // ---------------- fill warps ---------------------------------------------
     const int e = tid - NCW * 32;
@@ -421,8 +433,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       __syncthreads();               // A: collision loads of plane m done
       if constexpr (CL) __syncthreads();  // C: learned closure done
       if (m + 2 <= m1) fill(e, m + 2);  // overlaps the collision of plane m
-      __syncthreads();               // B
+      if constexpr (NBUF == 1) __syncthreads();  // B
     }
+    if constexpr (NBUF == 2) __syncthreads();  // tile done (shared memory reuse)
     return;
   }
   if (!FW) {
@@ -518,14 +531,14 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       R a = R(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) a += hv[i];
-      sAd[k][node] = a;
+      sAd[m & (NBUF - 1)][k][node] = a;
       R pf = R(0);
 #pragma unroll
       for (int j = 0; j < NFM; ++j) {
         const int i = k + j * C;
         if (i != 0 && i < Q) pf += fo[j];
       }
-      sPf[k][node] = pf;
+      sPf[m & (NBUF - 1)][k][node] = pf;
     }
     if constexpr (!FW) {
       if (fslot) fill_store(tid, fok, mn, fgx, fgy, fn, m + 1);
@@ -568,7 +581,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           }
 #pragma unroll
           for (int q = 0; q < C; ++q) {
-            Ad[q] = sAd[q][node];
+            Ad[q] = sAd[m & (NBUF - 1)][q][node];
             A[q] = Ad[q] + (diag<L>(q) ? R(1) : R(0));
           }
           int q = 0;
@@ -622,10 +635,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       for (int a = 0; a < D; ++a) u[a] = ring[rc][a][e_own];
       R Ad[C];
 #pragma unroll
-      for (int q = 0; q < C; ++q) Ad[q] = sAd[q][node];
+      for (int q = 0; q < C; ++q) Ad[q] = sAd[m & (NBUF - 1)][q][node];
       R sumf = R(0);
 #pragma unroll
-      for (int q = 0; q < C; ++q) sumf += sPf[q][node];
+      for (int q = 0; q < C; ++q) sumf += sPf[m & (NBUF - 1)][q][node];
       R F[3];
       body_force<L, R>(ph, x, D == 3 ? y : m, F);
       R uu = R(0), Fu = R(0);
@@ -775,8 +788,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         }
       }
     }
-    __syncthreads();                    // B
+    if constexpr (NBUF == 1) __syncthreads();  // B
   }
+  if constexpr (NBUF == 2) __syncthreads();  // tile done (shared memory reuse)
 }
 
 template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL = false>
