@@ -32,7 +32,9 @@ using RT = typename Store<S>::R;
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if constexpr (BYTES == 8)
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+  else if constexpr (BYTES == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
@@ -323,24 +325,32 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   static_assert(FW || NE <= NCW * 32, "in-collision fill: one ring slot per thread");
   using CLS = typename std::conditional<CL, ClosureSmem<NG, C, NS>, NoClosureSmem>::type;
   // Prefetch of the next plane's populations of each collision thread
-  // (Q stress populations, its flow populations and chi) with cp.async,
-  // double-buffered; FP32 storage (4-byte copies; the stage then fits the
-  // 48 KB of static shared memory), not with the learned closure.
-  constexpr bool PF = sizeof(S) == 4 && !CL;
-  constexpr int NPF = Q + NFM + 1;
+  // (Q stress populations and its flow populations; chi apart, in its own
+  // type) with cp.async, double-buffered.  FP32 storage copies one element
+  // per thread; 16-bit storage copies 4-byte pairs, the even lane of a pair
+  // the even-numbered populations of both nodes and the odd lane the odd
+  // ones (needs 4-byte-aligned pairs: nx even, checked at run time).  Not
+  // for FP64 (the stage would not fit the 48 KB of static shared memory)
+  // nor with the learned closure.
+  constexpr bool PF = (sizeof(S) == 4 || sizeof(S) == 2) && !CL;
+  constexpr bool PAIR = sizeof(S) == 2;
+  constexpr int NPP = Q + NFM;
   constexpr int NCT = NCW * 32;
-  using Stage = typename std::conditional<PF, S[2][NPF][NCT], int>::type;
+  using Stage = typename std::conditional<PF, S[2][NPP][NCT], int>::type;
+  using StageX = typename std::conditional<PF, X[2][NCT], int>::type;
   // The exchange arrays sAd / sPf are double-buffered by plane parity when
   // static shared memory allows: plane m + 1 then writes the other copy
   // while slower warps still read plane m's, and one barrier per plane
   // suffices (otherwise a second barrier closes each plane).
-  constexpr size_t kSmemOne = sizeof(R) * 4 * D * NE + sizeof(CLS) + sizeof(Stage);
+  constexpr size_t kSmemOne =
+      sizeof(R) * 4 * D * NE + sizeof(CLS) + sizeof(Stage) + sizeof(StageX);
   constexpr int NBUF = (kSmemOne + 2 * 2 * sizeof(R) * C * NS <= 48 * 1024) ? 2 : 1;
   __shared__ R ring[4][D][NE];          // velocity of planes m-1 .. m+2
   __shared__ R sAd[NBUF][C][NS];        // A - I of the tile nodes
   __shared__ R sPf[NBUF][C][NS];        // partial sums of f_{i != 0}
   __shared__ CLS cls;                   // learned closure (CL only)
-  __shared__ Stage stage;
+  __shared__ __align__(16) Stage stage;
+  __shared__ __align__(16) StageX stage_x;
   static_assert(!CL || std::is_same<R, float>::value, "the learned closure runs in FP32");
 
   const int nx = g.nx, ny = g.ny;
@@ -402,6 +412,12 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   // measured faster there than holding it in registers)
   int sgx = 0, sgy = 0;
   const bool shas = FW && filler && slot_node(tid - NCW * 32, sgx, sgy);
+  auto fill_load = [&](bool ok, int mm, int gx, int gy, R (&fv)[Q]) {
+    if (ok) {
+      const long long s = (D == 3) ? ((long long)mm * ny + gy) * nx + gx : (long long)mm * nx + gx;
+      load_f<L, S>(b.f_in, P, s, fv);
+    }
+  };
   auto fill = [&](int e, int q) {
     if (e >= NE) return;
     int gx = sgx, gy = sgy;
@@ -409,10 +425,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     const int mm = plane_of(q);
     const bool ok = has && mm >= 0;
     R fv[Q];
-    if (ok) {
-      const long long s = (D == 3) ? ((long long)mm * ny + gy) * nx + gx : (long long)mm * nx + gx;
-      load_f<L, S>(b.f_in, P, s, fv);
-    }
+    fill_load(ok, mm, gx, gy, fv);
     fill_store(e, ok, mm, gx, gy, fv, q);
   };
 
@@ -424,15 +437,28 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   // m - 1, which every warp finished before A(m).
   if (FW && filler) {
     // ---------------- fill warps ---------------------------------------------
+    // The populations of the next plane to fill are loaded one plane ahead
+    // (held in registers across the barrier), so a plane's fill costs the
+    // velocity arithmetic only and the DRAM latency hides behind the
+    // collision of the plane before.
     const int e = tid - NCW * 32;
     fill(e, m0 - 1);
     fill(e, m0);
     fill(e, m0 + 1);
+    R fv[Q];
+    int mq = plane_of(m0 + 2);
+    bool okq = shas && mq >= 0;
+    if (m0 + 2 <= m1) fill_load(okq, mq, sgx, sgy, fv);
     __syncthreads();
     for (int m = m0; m < m1; ++m) {
       __syncthreads();               // A: collision loads of plane m done
       if constexpr (CL) __syncthreads();  // C: learned closure done
-      if (m + 2 <= m1) fill(e, m + 2);  // overlaps the collision of plane m
+      if (m + 2 <= m1 && e < NE) {   // overlaps the collision of plane m
+        fill_store(e, okq, mq, sgx, sgy, fv, m + 2);
+        mq = plane_of(m + 3);
+        okq = shas && mq >= 0;
+        if (m + 3 <= m1) fill_load(okq, mq, sgx, sgy, fv);
+      }
       if constexpr (NBUF == 1) __syncthreads();  // B
     }
     if constexpr (NBUF == 2) __syncthreads();  // tile done (shared memory reuse)
@@ -465,21 +491,66 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   const int oy_p = (D == 3) ? ((y == ny - 1) ? -(ny - 1) * nx : nx) : 0;
   const int oy_m = (D == 3) ? ((y == 0) ? (ny - 1) * nx : -nx) : 0;
   // issue the copies of plane q's populations into stage buffer q & 1
+  const bool pf = PF && (!PAIR || (nx & 1) == 0);
+  const unsigned amask = __ballot_sync(0xffffffffu, active);  // all 32 lanes are here
+  // Whole rows: when all 32 nodes of the warp are in the grid and a row of
+  // them starts on a 16-byte boundary (nx a multiple of 16 bytes' worth of
+  // elements; pitch and array bases are), the warp copies its rows in
+  // 16-byte chunks, spread over the lanes, instead of one element per lane.
+  constexpr int EPC = 16 / (int)sizeof(S);     // elements per chunk
+  constexpr bool WIDE = D == 3 || sizeof(S) == 2;
+  const bool wide = PF && WIDE && amask == 0xffffffffu && (nx % EPC) == 0;
   auto prefetch = [&](int q) {
     if constexpr (PF) {
-      if (!active || q >= m1) return;
+      if (!pf || !active || q >= m1) return;
       const long long sq = (D == 3) ? ((long long)q * ny + y) * nx + x : (long long)q * nx + x;
       const uint32_t sq32 = (uint32_t)sq;
       const int st = q & 1;
+      if (wide) {
+        constexpr int CPR = 32 / EPC;          // chunks per row of 32 nodes
+        constexpr int NCP = NPP * CPR;         // population chunks
+        constexpr int NCH = NCP + 32 * 4 / 16; // and chi (4-byte) chunks
+        const uint32_t s0 = sq32 - (uint32_t)lane;  // node of lane 0
+        const int wb = tid - lane;             // the warp's stage columns
 #pragma unroll
-      for (int i = 0; i < Q; ++i) cp_async<sizeof(S)>(&stage[st][i][tid], hin_k + ((uint32_t)i * P32 + sq32));
-#pragma unroll
-      for (int j = 0; j < NFM; ++j) {
-        const int i = k + j * C;
-        if (i < Q) cp_async<sizeof(S)>(&stage[st][Q + j][tid], b.f_in + ((uint32_t)i * P32 + sq32));
+        for (int jj = 0; jj < (NCH + 31) / 32; ++jj) {
+          const int c = lane + 32 * jj;
+          if (c < NCP) {
+            const int v = c / CPR, sub = c % CPR;
+            const int i = v < Q ? v : k + (v - Q) * C;
+            const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + s0 + (uint32_t)(sub * EPC));
+            if (i < Q) cp_async<16>(&stage[st][v][wb + sub * EPC], src);
+          } else if (c < NCH) {
+            const int sub = c - NCP;
+            cp_async<16>(&stage_x[st][wb + sub * 4], b.chi + ((uint32_t)k * P32 + s0 + (uint32_t)(sub * 4)));
+          }
+        }
+        cp_commit();
+        return;
       }
-      if (sizeof(X) == sizeof(S))
-        cp_async<sizeof(S)>(&stage[st][Q + NFM][tid], b.chi + ((uint32_t)k * P32 + sq32));
+      if constexpr (PAIR) {
+        // lanes 2j, 2j + 1 hold nodes sq, sq + 1 (x even, nx even)
+        const int par = tid & 1;
+        const int tb = tid - par;
+        const uint32_t sp = sq32 - (uint32_t)par;
+#pragma unroll
+        for (int jj = 0; jj < (NPP + 1) / 2; ++jj) {
+          const int v = 2 * jj + par;
+          const int i = v < Q ? v : k + (v - Q) * C;
+          const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + sp);
+          if (v < NPP && i < Q) cp_async<4>(&stage[st][v][tb], src);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) cp_async<4>(&stage[st][i][tid], hin_k + ((uint32_t)i * P32 + sq32));
+#pragma unroll
+        for (int j = 0; j < NFM; ++j) {
+          const int i = k + j * C;
+          if (i < Q) cp_async<4>(&stage[st][Q + j][tid], b.f_in + ((uint32_t)i * P32 + sq32));
+        }
+      }
+      static_assert(sizeof(X) == 4, "chi is staged in 4-byte copies");
+      cp_async<4>(&stage_x[st][tid], b.chi + ((uint32_t)k * P32 + sq32));
       cp_commit();
     }
   };
@@ -508,17 +579,28 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     R hv[Q], fo[NFM];
     R old = R(0);
     if (active) {
+      bool staged = false;
       if constexpr (PF) {
-        // this plane's copies (issued one plane ago); then start the next
-        cp_wait_all();
-        const int st = m & 1;
+        if (pf) {
+          // this plane's copies (issued one plane ago); then start the next.
+          // Whole-row chunks and a pair's copies were issued by other lanes
+          // too: the active lanes synchronise after the wait so that each
+          // sees the others' (both lanes of a pair are active or neither is;
+          // whole rows imply all 32 lanes).
+          cp_wait_all();
+          if (PAIR || wide) __syncwarp(amask);
+          const int st = m & 1;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) hv[i] = R(stage[st][i][tid]);
+          for (int i = 0; i < Q; ++i) hv[i] = Store<S>::cvt(stage[st][i][tid]);
 #pragma unroll
-        for (int j = 0; j < NFM; ++j) fo[j] = (k + j * C < Q) ? R(stage[st][Q + j][tid]) : R(0);
-        old = sizeof(X) == sizeof(S) ? R(stage[st][Q + NFM][tid]) : R(b.chi[(uint32_t)k * P32 + s32]);
-        prefetch(m + 1);
-      } else {
+          for (int j = 0; j < NFM; ++j)
+            fo[j] = (k + j * C < Q) ? Store<S>::cvt(stage[st][Q + j][tid]) : R(0);
+          old = R(stage_x[st][tid]);
+          prefetch(m + 1);
+          staged = true;
+        }
+      }
+      if (!staged) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) hv[i] = Store<S>::ld(hin_k + ((uint32_t)i * P32 + s32));
 #pragma unroll

@@ -104,6 +104,7 @@ struct Store<double> {
   using R = double;     // arithmetic
   using X = double;     // chi of the previous step
   __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
+  __device__ static __forceinline__ double cvt(double v) { return v; }
   static constexpr bool sr = false;
   __device__ static __forceinline__ void st(double* p, double v, uint32_t) { *p = v; }
   __device__ static __forceinline__ double ld_l2(const double* p) {
@@ -118,6 +119,7 @@ struct Store<float> {
   using R = float;
   using X = float;
   __device__ static __forceinline__ float ld(const float* p) { return __ldg(p); }
+  __device__ static __forceinline__ float cvt(float v) { return v; }
   static constexpr bool sr = false;
   __device__ static __forceinline__ void st(float* p, float v, uint32_t) { *p = v; }
   __device__ static __forceinline__ float ld_l2(const float* p) {
@@ -135,6 +137,7 @@ struct Store<__half> {
   __device__ static __forceinline__ float ld(const __half* p) {
     return __half2float(__ldg(p));
   }
+  __device__ static __forceinline__ float cvt(__half v) { return __half2float(v); }
   __device__ static __forceinline__ void st(__half* p, float v, uint32_t) {
     *p = __float2half_rn(v);
   }
@@ -151,6 +154,7 @@ struct Store<__nv_bfloat16> {
   __device__ static __forceinline__ float ld(const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(p));
   }
+  __device__ static __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, uint32_t) {
     *p = __float2bfloat16_rn(v);
   }
@@ -179,6 +183,9 @@ struct Store<half_sr> {
   __device__ static __forceinline__ float ld(const half_sr* p) {
     return __half2float(__ushort_as_half(__ldg(&p->b)));
   }
+  __device__ static __forceinline__ float cvt(half_sr v) {
+    return __half2float(__ushort_as_half(v.b));
+  }
   // r: 32 random bits.  Add r * ulp(|v|) in magnitude, then truncate.
   __device__ static __forceinline__ void st(half_sr* p, float v, uint32_t r) {
     const uint32_t bits = __float_as_uint(v);
@@ -202,6 +209,7 @@ struct Store<bf16_sr> {
   __device__ static __forceinline__ float ld(const bf16_sr* p) {
     return __uint_as_float((uint32_t)__ldg(&p->b) << 16);
   }
+  __device__ static __forceinline__ float cvt(bf16_sr v) { return __uint_as_float((uint32_t)v.b << 16); }
   // add 16 random bits below the kept 16 and truncate (sign-magnitude, so the
   // rounding is unbiased in magnitude and hence in value)
   __device__ static __forceinline__ void st(bf16_sr* p, float v, uint32_t r) {

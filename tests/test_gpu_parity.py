@@ -148,6 +148,34 @@ def test_reduced_precision_taylor_green(prec, bu, bt):
     assert w["u"] <= bu and w["tau_p"] <= bt, w
 
 
+# 16-bit storage on ragged grids.  A warp whose 32 nodes are all in the grid
+# with nx a multiple of 8 copies whole rows in 16-byte chunks; otherwise,
+# with nx even, the fused kernel stages the populations of each pair of
+# neighbouring nodes with 4-byte copies shared by the pair's two lanes (a
+# tile's ragged tail leaves part of a warp without nodes); with nx odd it
+# loads them directly.  An exchanged or misplaced chunk or half of a pair
+# gives errors of order one; the bounds are those of the 16-bit forms above
+# for a short horizon.
+RAGGED16 = [((34, 5, 6), 0b001), ((37, 4, 5), 0b010), ((66, 3, 4), 0), ((40, 5, 4), 0b100),
+            ((66, 9), 0b01), ((33, 17), 0b10), ((130, 5), 0), ((136, 9), 0b01)]
+
+
+@pytest.mark.parametrize("prec,bu,bt", [(FP16, 2e-3, 4e-3), (BF16SR, 1.5e-2, 3e-2)])
+@pytest.mark.parametrize("shape,walls", RAGGED16)
+def test_ragged_16bit(prec, bu, bt, shape, walls):
+    if len(shape) == 3:
+        nx, ny, nz = shape
+        pr = W.Problem("r3", W.D3Q19, nx, ny, nz, 0.75, 0.1, 13.0, W.FORCE_CONST,
+                       (1e-5, 2e-5, -1e-5), walls=walls)
+    else:
+        nx, ny = shape
+        pr = W.Problem("r", W.D2Q9, nx, ny, 1, 0.7, 0.15, 11.0, W.FORCE_CONST,
+                       (1e-5, -2e-5, 0.0), walls=walls)
+    _with_random(pr, seed=sum(shape) + walls)
+    w = compare(pr, 20, prec, 1.0, chunks=2, fields=("u", "tau_p"))
+    assert w["u"] <= bu and w["tau_p"] <= bt, w
+
+
 # ---------------------------------------------------------------------------
 # Full-size launch configurations, checked through periodic tiling: a
 # problem whose fields repeat with the period of a small grid evolves as the
