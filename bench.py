@@ -198,6 +198,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def kernel_label(lattice: str, precision: str) -> str:
+    """The fused-step kernel instance the library launches for this workload."""
+    S = {"fp64": "double", "fp32": "float", "fp16_dev": "__half", "bf16_dev": "__nv_bfloat16",
+         "fp16_dev_sr": "half_sr", "bf16_dev_sr": "bf16_sr"}[precision]
+    minb = 1 if precision == "fp64" else 2
+    if lattice == "d2q9":
+        return (f"k_step_fused<D2Q9,{S},GX=4,TY=1,MINB={minb},periodic> "
+                f"(128 nodes x 3 stress components per block, in-warp halo fill)")
+    return (f"k_step_fused<D3Q19,{S},GX=1,TY=1,MINB={minb},periodic,fill warps> "
+            f"(32 nodes x 6 stress components + 4 halo fill warps per block)")
+
+
 def config_dict(args=None, note=""):
     w = WORKLOAD
     prec = args.precision if args else "fp32"
@@ -431,7 +443,7 @@ def run_ours(args, rank, world, dist):
                      "traffic": tr["dram_bytes_per_launch"] if tr else None,
                      "algorithmic_bytes_per_launch": bpu * sites,
                      "bytes_per_update": bpu, "peak_source": f"{which} hbm_gbs (copy)",
-                     "kernel": "k_step_fused<D3Q19,float,GX=1,TY=2> (32x2 nodes x 6 components)"},
+                     "kernel": kernel_label(args.lattice, args.precision)},
         "e2e": {"value": round(sites * e2e_steps / e2e_dt / 1e6, 1), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "fvlb_init_fields from host + K steps + fvlb_fields(U) to host"},

@@ -576,31 +576,48 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 #pragma unroll
       for (int i = 0; i < (FW ? 1 : Q); ++i) fn[i] = Store<S>::ld(b.f_in + i * P + sn);
     }
-    R hv[Q], fo[NFM];
+    // Staged storage types keep this plane's values in stage buffer m & 1
+    // until the collision has used them (read there again rather than held
+    // in registers across the barrier); FP64 and the learned-closure kernel
+    // hold them in registers.
+    const int st = m & 1;
+    R hv[PF ? 1 : Q], fo[PF ? 1 : NFM];
     R old = R(0);
     if (active) {
-      bool staged = false;
+      R a = R(0), psum = R(0);
       if constexpr (PF) {
         if (pf) {
           // this plane's copies (issued one plane ago); then start the next.
           // Whole-row chunks and a pair's copies were issued by other lanes
           // too: the active lanes synchronise after the wait so that each
           // sees the others' (both lanes of a pair are active or neither is;
-          // whole rows imply all 32 lanes).
+          // whole rows imply all 32 lanes).  The same synchronisation tells
+          // them that every lane has finished the collision of plane m - 1,
+          // whose buffer the next copies overwrite.
           cp_wait_all();
           if (PAIR || wide) __syncwarp(amask);
-          const int st = m & 1;
-#pragma unroll
-          for (int i = 0; i < Q; ++i) hv[i] = Store<S>::cvt(stage[st][i][tid]);
-#pragma unroll
-          for (int j = 0; j < NFM; ++j)
-            fo[j] = (k + j * C < Q) ? Store<S>::cvt(stage[st][Q + j][tid]) : R(0);
-          old = R(stage_x[st][tid]);
           prefetch(m + 1);
-          staged = true;
+        } else {
+          // no copies for this kernel: the node's own values into its own
+          // stage column
+#pragma unroll
+          for (int i = 0; i < Q; ++i) stage[st][i][tid] = hin_k[(uint32_t)i * P32 + s32];
+#pragma unroll
+          for (int j = 0; j < NFM; ++j) {
+            const int i = k + j * C;
+            if (i < Q) stage[st][Q + j][tid] = b.f_in[(uint32_t)i * P32 + s32];
+          }
+          stage_x[st][tid] = b.chi[(uint32_t)k * P32 + s32];
         }
-      }
-      if (!staged) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) a += Store<S>::cvt(stage[st][i][tid]);
+#pragma unroll
+        for (int j = 0; j < NFM; ++j) {
+          const int i = k + j * C;
+          if (i != 0 && i < Q) psum += Store<S>::cvt(stage[st][Q + j][tid]);
+        }
+        old = R(stage_x[st][tid]);
+      } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) hv[i] = Store<S>::ld(hin_k + ((uint32_t)i * P32 + s32));
 #pragma unroll
@@ -609,18 +626,16 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           fo[j] = i < Q ? Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s32)) : R(0);
         }
         old = R(b.chi[(uint32_t)k * P32 + s32]);
-      }
-      R a = R(0);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) a += hv[i];
+        for (int i = 0; i < Q; ++i) a += hv[i];
+#pragma unroll
+        for (int j = 0; j < NFM; ++j) {
+          const int i = k + j * C;
+          if (i != 0 && i < Q) psum += fo[j];
+        }
+      }
       sAd[m & (NBUF - 1)][k][node] = a;
-      R pf = R(0);
-#pragma unroll
-      for (int j = 0; j < NFM; ++j) {
-        const int i = k + j * C;
-        if (i != 0 && i < Q) pf += fo[j];
-      }
-      sPf[m & (NBUF - 1)][k][node] = pf;
+      sPf[m & (NBUF - 1)][k][node] = psum;
     }
     if constexpr (!FW) {
       if (fslot) fill_store(tid, fok, mn, fgx, fgy, fn, m + 1);
@@ -838,7 +853,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if (c == 1) cu += u[a];
           if (c == -1) cu -= u[a];
         }
-        const R post = keep * hv[i] + R(L::w(i)) * (alpha + cu * beta);
+        R hvi;
+        if constexpr (PF) hvi = Store<S>::cvt(stage[st][i][tid]);
+        else hvi = hv[i];
+        const R post = keep * hvi + R(L::w(i)) * (alpha + cu * beta);
         int j;
         const uint32_t d = dest(i, j);
         Store<S>::st(hout_k + ((uint32_t)j * P32 + d), post, Store<S>::sr ? lcg_next(rng) : 0u);
@@ -863,7 +881,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
           const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
           const R fBi = fB_dir<L, R>(i, Ad, kB);
-          const R post = fo[jj] - (fo[jj] - feq) * ph.inv_tau_f + fBi + Fi;
+          R foi;
+          if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][tid]);
+          else foi = fo[jj];
+          const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
           int j;
           const uint32_t d = dest(i, j);
           Store<S>::st(b.f_out + ((uint32_t)j * P32 + d), post, Store<S>::sr ? lcg_next(rng) : 0u);

@@ -103,8 +103,9 @@ cudaError_t step_impl(const StepDesc& d) {
             static_cast<X*>(d.chi)};
   if (d.variant == 0) {
     // Shapes measured fastest on GB300 (256^3 D3Q19, 2048^2 D2Q9): 2D four
-    // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D 32 x 2
-    // nodes x 6 components (384 threads).
+    // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D one
+    // 32-node row x 6 components + 4 halo fill warps (320 threads, 2 blocks
+    // per SM; a 64-register cap for 3 blocks per SM measured slower).
     constexpr bool wide = sizeof(RT<S>) == 8;
     if constexpr (L::D == 2) {
       // 4 groups x 3 components, ring filled by the collision threads
