@@ -278,6 +278,20 @@ struct Split {
   static constexpr int NFMAX = (L::Q + L::C - 1) / L::C;
 };
 
+// Call fn(std::integral_constant<int, k>) for a run-time component index
+// k < 6 (the callee ignores k >= its lattice's C).
+template <class Fn>
+__device__ __forceinline__ void on_component(int k, Fn&& fn) {
+  switch (k) {
+    case 0: fn(std::integral_constant<int, 0>{}); break;
+    case 1: fn(std::integral_constant<int, 1>{}); break;
+    case 2: fn(std::integral_constant<int, 2>{}); break;
+    case 3: fn(std::integral_constant<int, 3>{}); break;
+    case 4: fn(std::integral_constant<int, 4>{}); break;
+    default: fn(std::integral_constant<int, 5>{}); break;
+  }
+}
+
 // FW: dedicated fill warps computing the ring one plane ahead (D3Q19, where
 // a halo velocity costs 19 loads), or the ring filled by the first NE
 // collision threads in their own memory phase (D2Q9, 9 loads).
@@ -488,6 +502,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   // periodic neighbour offsets along x and y (constant over the march)
   const int ox_p = (x == nx - 1) ? -(nx - 1) : 1;
   const int ox_m = (x == 0) ? (nx - 1) : -1;
+  const uint32_t wxp = (x == nx - 1) ? (uint32_t)(-nx) : 0u;  // wrap corrections
+  const uint32_t wxm = (x == 0) ? (uint32_t)nx : 0u;
   const int oy_p = (D == 3) ? ((y == ny - 1) ? -(ny - 1) * nx : nx) : 0;
   const int oy_m = (D == 3) ? ((y == 0) ? (ny - 1) * nx : -nx) : 0;
   // issue the copies of plane q's populations into stage buffer q & 1
@@ -752,52 +768,54 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                   (sumf + R(-1.5 * w0) * uu + ph.tau_f * (R(-3.0 * w0) * ph.kf * Fu) +
                    ph.tau_f * fB0);
 
+      // Work that depends on the stress component k is dispatched once on
+      // k (warp-uniform), so that every population index and coefficient
+      // in it is a compile-time constant.
       // stress source of this component (Sec. 2.3):
       // chi_ab = -(A - I)_ab / lambda + sum_r (A_ar d_r u_b + d_r u_a A_rb)
       R chi_k = R(0), Ad_k = R(0), A_k = R(0);
-#pragma unroll
-      for (int q = 0; q < C; ++q) {
-        if (q != k) continue;
-        if constexpr (CL) {
-          chi_k = cls.chi[q][node];
+      on_component(k, [&](auto KC) {
+        constexpr int q = decltype(KC)::value;
+        if constexpr (q < C) {
           Ad_k = Ad[q];
           A_k = Ad[q] + (diag<L>(q) ? R(1) : R(0));
-          continue;
-        }
-        const int a = L::ca(q), bb = L::cb(q);
-        R v = -Ad[q] * ph.inv_lam;
+          if constexpr (CL) {
+            chi_k = cls.chi[q][node];
+          } else {
+            constexpr int a = L::ca(q), bb = L::cb(q);
+            R v = -Ad[q] * ph.inv_lam;
 #pragma unroll
-        for (int r = 0; r < D; ++r) {
-          // d_r u_a and d_r u_b from the ring (central, or one-sided at walls)
-          R dua, dub;
-          {
-            int e_p, e_m, r_p, r_m;
-            bool lo, hi;
-            if (r == 0) {
-              e_p = e_own + 1; e_m = e_own - 1; r_p = rc; r_m = rc;
-              lo = wall_x && x == 0; hi = wall_x && x == nx - 1;
-            } else if (r == 1 && D == 3) {
-              e_p = e_own + EX; e_m = e_own - EX; r_p = rc; r_m = rc;
-              lo = wall_y && y == 0; hi = wall_y && y == ny - 1;
-            } else {
-              e_p = e_own; e_m = e_own; r_p = rp; r_m = rm;
-              lo = wall_m && m == 0; hi = wall_m && m == nm - 1;
+            for (int r = 0; r < D; ++r) {
+              // d_r u_a and d_r u_b from the ring (central, or one-sided at walls)
+              R dua, dub;
+              {
+                int e_p, e_m, r_p, r_m;
+                bool lo, hi;
+                if (r == 0) {
+                  e_p = e_own + 1; e_m = e_own - 1; r_p = rc; r_m = rc;
+                  lo = wall_x && x == 0; hi = wall_x && x == nx - 1;
+                } else if (r == 1 && D == 3) {
+                  e_p = e_own + EX; e_m = e_own - EX; r_p = rc; r_m = rc;
+                  lo = wall_y && y == 0; hi = wall_y && y == ny - 1;
+                } else {
+                  e_p = e_own; e_m = e_own; r_p = rp; r_m = rm;
+                  lo = wall_m && m == 0; hi = wall_m && m == nm - 1;
+                }
+                const R pa = ring[r_p][a][e_p], ma = ring[r_m][a][e_m];
+                const R pb = ring[r_p][bb][e_p], mb = ring[r_m][bb][e_m];
+                dua = R(0.5) * (pa - ma);
+                dub = R(0.5) * (pb - mb);
+                if (lo) { dua = u[a] + pa * R(1.0 / 3.0); dub = u[bb] + pb * R(1.0 / 3.0); }
+                if (hi) { dua = -(u[a] + ma * R(1.0 / 3.0)); dub = -(u[bb] + mb * R(1.0 / 3.0)); }
+              }
+              const R Aar = Ad[sym<L>(a, r)] + (a == r ? R(1) : R(0));
+              const R Arb = Ad[sym<L>(r, bb)] + (r == bb ? R(1) : R(0));
+              v += Aar * dub + dua * Arb;
             }
-            const R pa = ring[r_p][a][e_p], ma = ring[r_m][a][e_m];
-            const R pb = ring[r_p][bb][e_p], mb = ring[r_m][bb][e_m];
-            dua = R(0.5) * (pa - ma);
-            dub = R(0.5) * (pb - mb);
-            if (lo) { dua = u[a] + pa * R(1.0 / 3.0); dub = u[bb] + pb * R(1.0 / 3.0); }
-            if (hi) { dua = -(u[a] + ma * R(1.0 / 3.0)); dub = -(u[bb] + mb * R(1.0 / 3.0)); }
+            chi_k = v;
           }
-          const R Aar = Ad[sym<L>(a, r)] + (a == r ? R(1) : R(0));
-          const R Arb = Ad[sym<L>(r, bb)] + (r == bb ? R(1) : R(0));
-          v += Aar * dub + dua * Arb;
         }
-        chi_k = v;
-        Ad_k = Ad[q];
-        A_k = Ad[q] + (diag<L>(q) ? R(1) : R(0));
-      }
+      });
       if (ph.first) old = chi_k;
       b.chi[(uint32_t)k * P32 + s32] = X(chi_k);
       const R src = R(1.5) * chi_k - R(0.5) * old;
@@ -837,6 +855,12 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         j = i;
         return (uint32_t)d;
       };
+      // Without walls, a warp whose row and plane wrap around no periodic
+      // boundary (all but the first and last rows and planes) finds the
+      // destination of direction i at the fixed distance
+      // i * pitch + c_x + c_y nx (+ c_z nx ny) from its node, plus nx or
+      // -nx for the lanes at the two ends of a row.
+      const bool fast = !WALLS && (D == 2 || (y > 0 && y < ny - 1)) && m > 0 && m < nm - 1;
 
       // h_k: h* = (1 - 1/tau_h) h + w_i [alpha + c_i.u beta] with
       // alpha = (A-I)_k / tau_h + src and beta = 3 (A_k / tau_h + kh src)
@@ -844,52 +868,66 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       const R alpha = om * Ad_k + src;
       const R beta = R(3) * (om * A_k + ph.kh * src);
       const R keep = R(1) - om;
+      auto emit = [&](auto FASTC) {
+        constexpr bool FAST = decltype(FASTC)::value;
+        auto index = [&](int i) -> uint32_t {
+          if constexpr (FAST) {
+            const int cx = L::cx(i);
+            const uint32_t xw = cx == 1 ? wxp : (cx == -1 ? wxm : 0u);
+            return s32 + (uint32_t)i * P32 + (uint32_t)(cx + L::cy(i) * nx + L::cz(i) * strm) + xw;
+          } else {
+            int j;
+            const uint32_t d = dest(i, j);
+            return (uint32_t)j * P32 + d;
+          }
+        };
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        R cu = R(0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          const int c = cc<L>(i, a);
-          if (c == 1) cu += u[a];
-          if (c == -1) cu -= u[a];
-        }
-        R hvi;
-        if constexpr (PF) hvi = Store<S>::cvt(stage[st][i][tid]);
-        else hvi = hv[i];
-        const R post = keep * hvi + R(L::w(i)) * (alpha + cu * beta);
-        int j;
-        const uint32_t d = dest(i, j);
-        Store<S>::st(hout_k + ((uint32_t)j * P32 + d), post, Store<S>::sr ? lcg_next(rng) : 0u);
-      }
-
-      // f_i, i = k (mod C): f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
-#pragma unroll
-      for (int jj = 0; jj < NFM; ++jj) {
-#pragma unroll
-        for (int kk = 0; kk < C; ++kk) {
-          const int i = kk + jj * C;
-          if (kk != k || i >= Q) continue;
-          R cu = R(0), cF = R(0);
+        for (int i = 0; i < Q; ++i) {
+          R cu = R(0);
 #pragma unroll
           for (int a = 0; a < D; ++a) {
             const int c = cc<L>(i, a);
-            if (c == 1) { cu += u[a]; cF += F[a]; }
-            if (c == -1) { cu -= u[a]; cF -= F[a]; }
+            if (c == 1) cu += u[a];
+            if (c == -1) cu -= u[a];
           }
-          const R wi = R(L::w(i));
-          const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
-          const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-          const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
-          const R fBi = fB_dir<L, R>(i, Ad, kB);
-          R foi;
-          if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][tid]);
-          else foi = fo[jj];
-          const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
-          int j;
-          const uint32_t d = dest(i, j);
-          Store<S>::st(b.f_out + ((uint32_t)j * P32 + d), post, Store<S>::sr ? lcg_next(rng) : 0u);
+          R hvi;
+          if constexpr (PF) hvi = Store<S>::cvt(stage[st][i][tid]);
+          else hvi = hv[i];
+          const R post = keep * hvi + R(L::w(i)) * (alpha + cu * beta);
+          Store<S>::st(hout_k + index(i), post, Store<S>::sr ? lcg_next(rng) : 0u);
         }
-      }
+
+        // f_i, i = k (mod C): f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
+        on_component(k, [&](auto KC) {
+          constexpr int kk = decltype(KC)::value;
+          if constexpr (kk < C) {
+#pragma unroll
+            for (int jj = 0; jj < NFM; ++jj) {
+              const int i = kk + jj * C;
+              if (i >= Q) continue;
+              R cu = R(0), cF = R(0);
+#pragma unroll
+              for (int a = 0; a < D; ++a) {
+                const int c = cc<L>(i, a);
+                if (c == 1) { cu += u[a]; cF += F[a]; }
+                if (c == -1) { cu -= u[a]; cF -= F[a]; }
+              }
+              const R wi = R(L::w(i));
+              const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
+              const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+              const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
+              const R fBi = fB_dir<L, R>(i, Ad, kB);
+              R foi;
+              if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][tid]);
+              else foi = fo[jj];
+              const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
+              Store<S>::st(b.f_out + index(i), post, Store<S>::sr ? lcg_next(rng) : 0u);
+            }
+          }
+        });
+      };
+      if (fast) emit(std::true_type{});
+      else emit(std::false_type{});
     }
     if constexpr (NBUF == 1) __syncthreads();  // B
   }
