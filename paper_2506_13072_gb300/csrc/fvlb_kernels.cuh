@@ -43,6 +43,11 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
+// wait until at most N of this thread's most recent groups are pending
+template <int N>
+__device__ __forceinline__ void cp_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Make a pointer opaque to the compiler at this point of the program.  Used
 // to stop the 114 population addresses of a D3Q19 site from being computed
@@ -278,6 +283,39 @@ struct Split {
   static constexpr int NFMAX = (L::Q + L::C - 1) / L::C;
 };
 
+// Velocity of a ring slot: the D components in one 16-byte (FP32) or
+// 32-byte (FP64) record, so a slot is read and written with vector
+// shared-memory accesses.
+template <class R, int D>
+struct alignas(sizeof(R) * (D == 3 ? 4 : 2)) Vel {
+  R v[D == 3 ? 4 : 2];
+};
+
+// out[0..N) = p[0..N) from shared memory, p 16-byte aligned, in 16- and
+// 8-byte pieces.
+template <class R, int N>
+__device__ __forceinline__ void lds_row(const R* p, R (&out)[N]) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int j = 0; j + 4 <= N; j += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p + j);
+      out[j] = t.x; out[j + 1] = t.y; out[j + 2] = t.z; out[j + 3] = t.w;
+    }
+    if constexpr (N % 4 >= 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p + N / 4 * 4);
+      out[N / 4 * 4] = t.x; out[N / 4 * 4 + 1] = t.y;
+    }
+    if constexpr (N % 2 == 1) out[N - 1] = p[N - 1];
+  } else {
+#pragma unroll
+    for (int j = 0; j + 2 <= N; j += 2) {
+      const double2 t = *reinterpret_cast<const double2*>(p + j);
+      out[j] = t.x; out[j + 1] = t.y;
+    }
+    if constexpr (N % 2 == 1) out[N - 1] = p[N - 1];
+  }
+}
+
 // Call fn(std::integral_constant<int, k>) for a run-time component index
 // k < 6 (the callee ignores k >= its lattice's C).
 template <class Fn>
@@ -350,18 +388,26 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   constexpr bool PAIR = sizeof(S) == 2;
   constexpr int NPP = Q + NFM;
   constexpr int NCT = NCW * 32;
-  using Stage = typename std::conditional<PF, S[2][NPP][NCT], int>::type;
-  using StageX = typename std::conditional<PF, X[2][NCT], int>::type;
+  // NST stage buffers: the copies run NST - 1 planes ahead of the
+  // collision (three where static shared memory allows, else two).
+  constexpr size_t kStage3 = PF ? 3 * (sizeof(S) * NPP * NCT + sizeof(X) * NCT) : 0;
+  constexpr size_t kSmem3 = sizeof(Vel<R, D>) * 4 * NE + sizeof(CLS) + kStage3 +
+                            2 * 2 * sizeof(R) * (C == 6 ? 8 : 4) * NS;
+  constexpr int NST = (PF && kSmem3 <= 48 * 1024) ? 3 : 2;
+  using Stage = typename std::conditional<PF, S[NST][NPP][NCT], int>::type;
+  using StageX = typename std::conditional<PF, X[NST][NCT], int>::type;
   // The exchange arrays sAd / sPf are double-buffered by plane parity when
   // static shared memory allows: plane m + 1 then writes the other copy
   // while slower warps still read plane m's, and one barrier per plane
   // suffices (otherwise a second barrier closes each plane).
+  // (node-major, each node's C values padded to CP for vector loads)
+  constexpr int CP = C == 6 ? 8 : 4;
   constexpr size_t kSmemOne =
-      sizeof(R) * 4 * D * NE + sizeof(CLS) + sizeof(Stage) + sizeof(StageX);
-  constexpr int NBUF = (kSmemOne + 2 * 2 * sizeof(R) * C * NS <= 48 * 1024) ? 2 : 1;
-  __shared__ R ring[4][D][NE];          // velocity of planes m-1 .. m+2
-  __shared__ R sAd[NBUF][C][NS];        // A - I of the tile nodes
-  __shared__ R sPf[NBUF][C][NS];        // partial sums of f_{i != 0}
+      sizeof(Vel<R, D>) * 4 * NE + sizeof(CLS) + sizeof(Stage) + sizeof(StageX);
+  constexpr int NBUF = (kSmemOne + 2 * 2 * sizeof(R) * CP * NS <= 48 * 1024) ? 2 : 1;
+  __shared__ Vel<R, D> ring[4][NE];     // velocity of planes m-1 .. m+2
+  __shared__ __align__(16) R sAd[NBUF][NS][CP];  // A - I of the tile nodes
+  __shared__ __align__(16) R sPf[NBUF][NS][CP];  // partial sums of f_{i != 0}
   __shared__ CLS cls;                   // learned closure (CL only)
   __shared__ __align__(16) Stage stage;
   __shared__ __align__(16) StageX stage_x;
@@ -416,9 +462,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       body_force<L, R>(ph, gx, D == 3 ? gy : mm, F);
       velocity<L, R>(fv, F, u);
     }
-    const int r = slot(q);
+    Vel<R, D> t;
 #pragma unroll
-    for (int a = 0; a < D; ++a) ring[r][a][e] = u[a];
+    for (int a = 0; a < (D == 3 ? 4 : 2); ++a) t.v[a] = a < D ? u[a] : R(0);
+    ring[slot(q)][e] = t;
   };
   // this thread's ring slot (fixed for the whole tile): node coordinates
   // computed once, outside the march
@@ -428,8 +475,11 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   const bool shas = FW && filler && slot_node(tid - NCW * 32, sgx, sgy);
   auto fill_load = [&](bool ok, int mm, int gx, int gy, R (&fv)[Q]) {
     if (ok) {
-      const long long s = (D == 3) ? ((long long)mm * ny + gy) * nx + gx : (long long)mm * nx + gx;
-      load_f<L, S>(b.f_in, P, s, fv);
+      // 32-bit offsets (Q * pitch < 2^32)
+      const uint32_t s = (D == 3) ? ((uint32_t)mm * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx
+                                  : (uint32_t)mm * (uint32_t)nx + (uint32_t)gx;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fv[i] = Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s));
     }
   };
   auto fill = [&](int e, int q) {
@@ -506,7 +556,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   const uint32_t wxm = (x == 0) ? (uint32_t)nx : 0u;
   const int oy_p = (D == 3) ? ((y == ny - 1) ? -(ny - 1) * nx : nx) : 0;
   const int oy_m = (D == 3) ? ((y == 0) ? (ny - 1) * nx : -nx) : 0;
-  // issue the copies of plane q's populations into stage buffer q & 1
+  // issue the copies of plane q's populations into stage buffer st
   const bool pf = PF && (!PAIR || (nx & 1) == 0);
   const unsigned amask = __ballot_sync(0xffffffffu, active);  // all 32 lanes are here
   // Whole rows: when all 32 nodes of the warp are in the grid and a row of
@@ -516,12 +566,18 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   constexpr int EPC = 16 / (int)sizeof(S);     // elements per chunk
   constexpr bool WIDE = D == 3 || sizeof(S) == 2;
   const bool wide = PF && WIDE && amask == 0xffffffffu && (nx % EPC) == 0;
-  auto prefetch = [&](int q) {
+  // Every call by a thread that stages commits exactly one group (empty
+  // past the end of the chunk), so a wait for all but the newest NST - 2
+  // groups completes plane m's copies.
+  auto prefetch = [&](int q, int st) {
     if constexpr (PF) {
-      if (!pf || !active || q >= m1) return;
+      if (!pf || !active) return;
+      if (q >= m1) {
+        cp_commit();
+        return;
+      }
       const long long sq = (D == 3) ? ((long long)q * ny + y) * nx + x : (long long)q * nx + x;
       const uint32_t sq32 = (uint32_t)sq;
-      const int st = q & 1;
       if (wide) {
         constexpr int CPR = 32 / EPC;          // chunks per row of 32 nodes
         constexpr int NCP = NPP * CPR;         // population chunks
@@ -570,7 +626,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       cp_commit();
     }
   };
-  prefetch(m0);
+  // stage buffers of plane m and of the plane NST - 1 ahead
+  int st = 0, st_ahead = NST - 1;
+  prefetch(m0, 0);
+  if constexpr (NST == 3) prefetch(m0 + 1, 1);
   __syncthreads();                      // ring prologue
 
   for (int m = m0; m < m1; ++m) {
@@ -592,11 +651,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 #pragma unroll
       for (int i = 0; i < (FW ? 1 : Q); ++i) fn[i] = Store<S>::ld(b.f_in + i * P + sn);
     }
-    // Staged storage types keep this plane's values in stage buffer m & 1
+    // Staged storage types keep this plane's values in stage buffer st
     // until the collision has used them (read there again rather than held
     // in registers across the barrier); FP64 and the learned-closure kernel
     // hold them in registers.
-    const int st = m & 1;
     R hv[PF ? 1 : Q], fo[PF ? 1 : NFM];
     R old = R(0);
     if (active) {
@@ -610,9 +668,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           // whole rows imply all 32 lanes).  The same synchronisation tells
           // them that every lane has finished the collision of plane m - 1,
           // whose buffer the next copies overwrite.
-          cp_wait_all();
+          if constexpr (NST == 3) cp_wait_group<1>();
+          else cp_wait_all();
           if (PAIR || wide) __syncwarp(amask);
-          prefetch(m + 1);
+          prefetch(m + NST - 1, st_ahead);
         } else {
           // no copies for this kernel: the node's own values into its own
           // stage column
@@ -650,8 +709,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if (i != 0 && i < Q) psum += fo[j];
         }
       }
-      sAd[m & (NBUF - 1)][k][node] = a;
-      sPf[m & (NBUF - 1)][k][node] = psum;
+      sAd[m & (NBUF - 1)][node][k] = a;
+      sPf[m & (NBUF - 1)][node][k] = psum;
     }
     if constexpr (!FW) {
       if (fslot) fill_store(tid, fok, mn, fgx, fgy, fn, m + 1);
@@ -669,23 +728,23 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         if (active) {
 #pragma unroll
           for (int bq = 0; bq < D; ++bq) {
-            const R uo = ring[rc][bq][e_own];
+            const R uo = ring[rc][e_own].v[bq];
             {
-              const R up = ring[rc][bq][e_own + 1], um = ring[rc][bq][e_own - 1];
+              const R up = ring[rc][e_own + 1].v[bq], um = ring[rc][e_own - 1].v[bq];
               R d = R(0.5) * (up - um);
               if (wall_x && x == 0) d = uo + up * R(1.0 / 3.0);
               if (wall_x && x == nx - 1) d = -(uo + um * R(1.0 / 3.0));
               gr[0][bq] = d;
             }
             if (D == 3) {
-              const R up = ring[rc][bq][e_own + EX], um = ring[rc][bq][e_own - EX];
+              const R up = ring[rc][e_own + EX].v[bq], um = ring[rc][e_own - EX].v[bq];
               R d = R(0.5) * (up - um);
               if (wall_y && y == 0) d = uo + up * R(1.0 / 3.0);
               if (wall_y && y == ny - 1) d = -(uo + um * R(1.0 / 3.0));
               gr[1][bq] = d;
             }
             {
-              const R up = ring[slot(m + 1)][bq][e_own], um = ring[slot(m - 1)][bq][e_own];
+              const R up = ring[slot(m + 1)][e_own].v[bq], um = ring[slot(m - 1)][e_own].v[bq];
               R d = R(0.5) * (up - um);
               if (wall_m && m == 0) d = uo + up * R(1.0 / 3.0);
               if (wall_m && m == nm - 1) d = -(uo + um * R(1.0 / 3.0));
@@ -694,7 +753,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           }
 #pragma unroll
           for (int q = 0; q < C; ++q) {
-            Ad[q] = sAd[m & (NBUF - 1)][q][node];
+            Ad[q] = sAd[m & (NBUF - 1)][node][q];
             A[q] = Ad[q] + (diag<L>(q) ? R(1) : R(0));
           }
           int q = 0;
@@ -744,14 +803,20 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     // ---- collision phase ------------------------------------------------------
     if (active) {
       R u[D];
+      {
+        const Vel<R, D> t = ring[rc][e_own];
 #pragma unroll
-      for (int a = 0; a < D; ++a) u[a] = ring[rc][a][e_own];
+        for (int a = 0; a < D; ++a) u[a] = t.v[a];
+      }
       R Ad[C];
-#pragma unroll
-      for (int q = 0; q < C; ++q) Ad[q] = sAd[m & (NBUF - 1)][q][node];
+      lds_row<R, C>(&sAd[m & (NBUF - 1)][node][0], Ad);
       R sumf = R(0);
+      {
+        R pf[C];
+        lds_row<R, C>(&sPf[m & (NBUF - 1)][node][0], pf);
 #pragma unroll
-      for (int q = 0; q < C; ++q) sumf += sPf[m & (NBUF - 1)][q][node];
+        for (int q = 0; q < C; ++q) sumf += pf[q];
+      }
       R F[3];
       body_force<L, R>(ph, x, D == 3 ? y : m, F);
       R uu = R(0), Fu = R(0);
@@ -801,8 +866,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                   e_p = e_own; e_m = e_own; r_p = rp; r_m = rm;
                   lo = wall_m && m == 0; hi = wall_m && m == nm - 1;
                 }
-                const R pa = ring[r_p][a][e_p], ma = ring[r_m][a][e_m];
-                const R pb = ring[r_p][bb][e_p], mb = ring[r_m][bb][e_m];
+                const Vel<R, D> vp = ring[r_p][e_p], vm = ring[r_m][e_m];
+                const R pa = vp.v[a], ma = vm.v[a];
+                const R pb = vp.v[bb], mb = vm.v[bb];
                 dua = R(0.5) * (pa - ma);
                 dub = R(0.5) * (pb - mb);
                 if (lo) { dua = u[a] + pa * R(1.0 / 3.0); dub = u[bb] + pb * R(1.0 / 3.0); }
@@ -893,7 +959,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           R hvi;
           if constexpr (PF) hvi = Store<S>::cvt(stage[st][i][tid]);
           else hvi = hv[i];
-          const R post = keep * hvi + R(L::w(i)) * (alpha + cu * beta);
+          const R wa = R(L::w(i)) * alpha, wb = R(L::w(i)) * beta;
+          const R post = keep * hvi + (wa + cu * wb);
           Store<S>::st(hout_k + index(i), post, Store<S>::sr ? lcg_next(rng) : 0u);
         }
 
@@ -930,6 +997,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       else emit(std::false_type{});
     }
     if constexpr (NBUF == 1) __syncthreads();  // B
+    st = st + 1 == NST ? 0 : st + 1;
+    st_ahead = st_ahead + 1 == NST ? 0 : st_ahead + 1;
   }
   if constexpr (NBUF == 2) __syncthreads();  // tile done (shared memory reuse)
 }
