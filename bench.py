@@ -206,6 +206,9 @@ def kernel_label(lattice: str, precision: str) -> str:
     if lattice == "d2q9":
         return (f"k_step_fused<D2Q9,{S},GX=4,TY=1,MINB={minb},periodic> "
                 f"(128 nodes x 3 stress components per block, in-warp halo fill)")
+    if precision == "fp32":
+        return (f"k_step_fused<D3Q19,float,GX=1,TY=1,MINB=2,periodic,fill warps,XN=2> "
+                f"(64 nodes x 6 stress components + 4 halo fill warps per block)")
     return (f"k_step_fused<D3Q19,{S},GX=1,TY=1,MINB={minb},periodic,fill warps> "
             f"(32 nodes x 6 stress components + 4 halo fill warps per block)")
 

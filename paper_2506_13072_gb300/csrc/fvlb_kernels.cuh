@@ -333,21 +333,22 @@ __device__ __forceinline__ void on_component(int k, Fn&& fn) {
 // FW: dedicated fill warps computing the ring one plane ahead (D3Q19, where
 // a halo velocity costs 19 loads), or the ring filled by the first NE
 // collision threads in their own memory phase (D2Q9, 9 loads).
-template <class L, int GX, int TY, bool FW>
+// XN: nodes per collision thread along x; a collision warp covers XN rows
+// of 32 consecutive nodes of one plane, one after the other (with fill
+// warps only).  Up to four fill warps, each thread filling SPF ring slots.
+template <class L, int GX, int TY, bool FW, int XN = 1>
 struct FusedShape {
-  static constexpr int NG = GX * TY;              // groups of 32 nodes per plane tile
+  static constexpr int NG = GX * TY;              // groups of 32 x XN nodes per plane tile
   static constexpr int NCW = NG * L::C;           // collision warps
-  static constexpr int TXS = GX * 32;             // tile extent along x
+  static constexpr int TXS = GX * 32 * XN;        // tile extent along x
   static constexpr int EX = TXS + 2;
   static constexpr int EY = (L::D == 3) ? TY + 2 : 1;
   static constexpr int NE = EX * EY;              // ring slots per plane
-  static constexpr int NFW = FW ? (NE + 31) / 32 : 0;  // fill warps
+  static constexpr int NFW = FW ? ((NE + 31) / 32 < 4 ? (NE + 31) / 32 : 4) : 0;  // fill warps
+  static constexpr int SPF = FW ? (NE + NFW * 32 - 1) / (NFW * 32) : 0;  // slots per fill thread
   static constexpr int NT = (NCW + NFW) * 32;     // threads
 };
 
-// One tile of the fused step: tile (bx, by) of the plane, chunk bz of the
-// march axis.  Called by k_step_fused (one tile per block) and by the
-// batched persistent kernel (many tiles of many grids per block).
 // Shared memory of the learned closure in a tile: the packed network, the
 // BF16 input rows and FP32 output rows of each group's warp, and the chosen
 // chi of every node.
@@ -362,56 +363,94 @@ struct NoClosureSmem {
   int unused;
 };
 
-template <class L, class S, int GX, int TY, bool WALLS, bool FW, bool CL = false>
+// Shared memory of one tile and the choices that depend on its size.
+//  - Stage (PF): the next planes' populations of every collision thread
+//    (Q stress populations and its flow populations; chi apart, in its own
+//    type), copied with cp.async: FP32 and 16-bit storage, not with the
+//    learned closure.  NST buffers: the copies run NST - 1 planes ahead of
+//    the collision (three where the budget allows, else two).
+//  - The exchange arrays sAd / sPf are double-buffered by plane parity where
+//    the budget allows: plane m + 1 then writes the other copy while slower
+//    warps still read plane m's, and one barrier per plane suffices
+//    (otherwise a second barrier closes each plane).  Node-major, each
+//    node's C values padded to CP for vector loads.
+// The budget is the 48 KB of static shared memory for one node per thread;
+// with more, the tile lives in dynamic shared memory sized for two blocks
+// per SM.
+template <class L, class S, int GX, int TY, bool FW, bool CL, int XN>
+struct TileCfg {
+  using R = RT<S>;
+  using X = typename Store<S>::X;
+  using Sh = FusedShape<L, GX, TY, FW, XN>;
+  static constexpr int D = L::D, Q = L::Q, C = L::C;
+  static constexpr int NS = Sh::NG * 32 * XN;     // nodes per plane tile
+  static constexpr int NFM = Split<L>::NFMAX;
+  static constexpr int NPP = Q + NFM;             // staged populations per thread
+  static constexpr int NCT = Sh::NCW * 32 * XN;   // stage columns
+  static constexpr int CP = C == 6 ? 8 : 4;
+  static constexpr bool PF = (sizeof(S) == 4 || sizeof(S) == 2) && !CL;
+  using CLS = typename std::conditional<CL, ClosureSmem<Sh::NG, C, NS>, NoClosureSmem>::type;
+  static constexpr size_t kRing = sizeof(Vel<R, D>) * 4 * Sh::NE;
+  static constexpr size_t kStage1 = PF ? sizeof(S) * NPP * NCT + sizeof(X) * NCT : 0;
+  static constexpr size_t kEx1 = 2 * sizeof(R) * CP * NS;
+  static constexpr bool kDynamic = XN > 1;
+  static constexpr size_t kLimit = kDynamic ? 110 * 1024 : 48 * 1024;
+  static constexpr int NST =
+      (PF && kRing + sizeof(CLS) + 3 * kStage1 + 2 * kEx1 <= kLimit) ? 3 : 2;
+  static constexpr int NBUF = (kRing + sizeof(CLS) + NST * kStage1 + 2 * kEx1 <= kLimit) ? 2 : 1;
+  using Stage = typename std::conditional<PF, S[NST][NPP][NCT], int>::type;
+  using StageX = typename std::conditional<PF, X[NST][NCT], int>::type;
+  struct Smem {
+    Vel<R, D> ring[4][Sh::NE];                    // velocity of planes m-1 .. m+2
+    alignas(16) R sAd[NBUF][NS][CP];              // A - I of the tile nodes
+    alignas(16) R sPf[NBUF][NS][CP];              // partial sums of f_{i != 0}
+    CLS cls;                                      // learned closure (CL only)
+    alignas(16) Stage stage;
+    alignas(16) StageX stage_x;
+  };
+  static constexpr size_t kDynamicBytes = kDynamic ? sizeof(Smem) : 0;
+};
+
+// One tile of the fused step: tile (bx, by) of the plane, chunk bz of the
+// march axis.  Called by k_step_fused (one tile per block) and by the
+// batched persistent kernel (many tiles of many grids per block).
+template <class L, class S, int GX, int TY, bool WALLS, bool FW, bool CL = false, int XN = 1>
 __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                                            const Bufs<S>& b, int mchunk, int bx, int by,
                                            int bz) {
   using R = RT<S>;
   using X = typename Store<S>::X;
-  using Sh = FusedShape<L, GX, TY, FW>;
+  using Sh = FusedShape<L, GX, TY, FW, XN>;
+  using Cfg = TileCfg<L, S, GX, TY, FW, CL, XN>;
   constexpr int D = L::D, Q = L::Q, C = L::C;
-  constexpr int NG = Sh::NG, NCW = Sh::NCW, TXS = Sh::TXS, EX = Sh::EX, NE = Sh::NE;
-  constexpr int NS = NG * 32;           // nodes per plane tile
-  constexpr int NFM = Split<L>::NFMAX;
+  constexpr int NCW = Sh::NCW, TXS = Sh::TXS, EX = Sh::EX, NE = Sh::NE;
+  constexpr int NFW = Sh::NFW, SPF = Sh::SPF;
+  constexpr int NFM = Cfg::NFM, NPP = Cfg::NPP, NST = Cfg::NST, NBUF = Cfg::NBUF;
+  constexpr bool PF = Cfg::PF;
+  constexpr bool PAIR = sizeof(S) == 2;
+  constexpr int WC = NCW * 32;          // stage columns of one node row
   static_assert(D == 3 || TY == 1, "2D tiles are one row high");
   static_assert(FW || NE <= NCW * 32, "in-collision fill: one ring slot per thread");
-  using CLS = typename std::conditional<CL, ClosureSmem<NG, C, NS>, NoClosureSmem>::type;
-  // Prefetch of the next plane's populations of each collision thread
-  // (Q stress populations and its flow populations; chi apart, in its own
-  // type) with cp.async, double-buffered.  FP32 storage copies one element
-  // per thread; 16-bit storage copies 4-byte pairs, the even lane of a pair
-  // the even-numbered populations of both nodes and the odd lane the odd
-  // ones (needs 4-byte-aligned pairs: nx even, checked at run time).  Not
-  // for FP64 (the stage would not fit the 48 KB of static shared memory)
-  // nor with the learned closure.
-  constexpr bool PF = (sizeof(S) == 4 || sizeof(S) == 2) && !CL;
-  constexpr bool PAIR = sizeof(S) == 2;
-  constexpr int NPP = Q + NFM;
-  constexpr int NCT = NCW * 32;
-  // NST stage buffers: the copies run NST - 1 planes ahead of the
-  // collision (three where static shared memory allows, else two).
-  constexpr size_t kStage3 = PF ? 3 * (sizeof(S) * NPP * NCT + sizeof(X) * NCT) : 0;
-  constexpr size_t kSmem3 = sizeof(Vel<R, D>) * 4 * NE + sizeof(CLS) + kStage3 +
-                            2 * 2 * sizeof(R) * (C == 6 ? 8 : 4) * NS;
-  constexpr int NST = (PF && kSmem3 <= 48 * 1024) ? 3 : 2;
-  using Stage = typename std::conditional<PF, S[NST][NPP][NCT], int>::type;
-  using StageX = typename std::conditional<PF, X[NST][NCT], int>::type;
-  // The exchange arrays sAd / sPf are double-buffered by plane parity when
-  // static shared memory allows: plane m + 1 then writes the other copy
-  // while slower warps still read plane m's, and one barrier per plane
-  // suffices (otherwise a second barrier closes each plane).
-  // (node-major, each node's C values padded to CP for vector loads)
-  constexpr int CP = C == 6 ? 8 : 4;
-  constexpr size_t kSmemOne =
-      sizeof(Vel<R, D>) * 4 * NE + sizeof(CLS) + sizeof(Stage) + sizeof(StageX);
-  constexpr int NBUF = (kSmemOne + 2 * 2 * sizeof(R) * CP * NS <= 48 * 1024) ? 2 : 1;
-  __shared__ Vel<R, D> ring[4][NE];     // velocity of planes m-1 .. m+2
-  __shared__ __align__(16) R sAd[NBUF][NS][CP];  // A - I of the tile nodes
-  __shared__ __align__(16) R sPf[NBUF][NS][CP];  // partial sums of f_{i != 0}
-  __shared__ CLS cls;                   // learned closure (CL only)
-  __shared__ __align__(16) Stage stage;
-  __shared__ __align__(16) StageX stage_x;
+  static_assert(XN == 1 || (FW && PF), "several nodes per thread: fill warps, staged storage");
   static_assert(!CL || std::is_same<R, float>::value, "the learned closure runs in FP32");
+  using Sm = typename Cfg::Smem;
+  Sm* smp;
+  if constexpr (Cfg::kDynamic) {
+    extern __shared__ __align__(16) unsigned char fvlb_tile_smem[];
+    smp = reinterpret_cast<Sm*>(fvlb_tile_smem);
+  } else {
+    __shared__ Sm tile_smem;
+    smp = &tile_smem;
+  }
+  auto& ring = smp->ring;
+  auto& sAd = smp->sAd;
+  auto& sPf = smp->sPf;
+  auto& cls = smp->cls;
+  auto& stage = smp->stage;
+  auto& stage_x = smp->stage_x;
+  (void)cls;
+  (void)stage;
+  (void)stage_x;
 
   const int nx = g.nx, ny = g.ny;
   const int nm = (D == 3) ? g.nz : g.ny;
@@ -467,12 +506,6 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     for (int a = 0; a < (D == 3 ? 4 : 2); ++a) t.v[a] = a < D ? u[a] : R(0);
     ring[slot(q)][e] = t;
   };
-  // this thread's ring slot (fixed for the whole tile): node coordinates
-  // computed once, outside the march
-  // (fill warps only; the in-collision fill recomputes it per plane, which
-  // measured faster there than holding it in registers)
-  int sgx = 0, sgy = 0;
-  const bool shas = FW && filler && slot_node(tid - NCW * 32, sgx, sgy);
   auto fill_load = [&](bool ok, int mm, int gx, int gy, R (&fv)[Q]) {
     if (ok) {
       // 32-bit offsets (Q * pitch < 2^32)
@@ -482,10 +515,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       for (int i = 0; i < Q; ++i) fv[i] = Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s));
     }
   };
-  auto fill = [&](int e, int q) {
+  // ring slot e of plane q, whose node (gx, gy) the caller found (`has`)
+  auto fill = [&](int e, bool has, int gx, int gy, int q) {
     if (e >= NE) return;
-    int gx = sgx, gy = sgy;
-    const bool has = FW ? shas : slot_node(e, gx, gy);
     const int mm = plane_of(q);
     const bool ok = has && mm >= 0;
     R fv[Q];
@@ -501,27 +533,47 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   // m - 1, which every warp finished before A(m).
   if (FW && filler) {
     // ---------------- fill warps ---------------------------------------------
-    // The populations of the next plane to fill are loaded one plane ahead
-    // (held in registers across the barrier), so a plane's fill costs the
-    // velocity arithmetic only and the DRAM latency hides behind the
-    // collision of the plane before.
-    const int e = tid - NCW * 32;
-    fill(e, m0 - 1);
-    fill(e, m0);
-    fill(e, m0 + 1);
-    R fv[Q];
+    // Each thread fills the ring slots e0 + t * 32 NFW, t < SPF; their node
+    // coordinates are fixed for the whole tile.  The populations of the next
+    // plane to fill are loaded one plane ahead (held in registers across the
+    // barrier), so a plane's fill costs the velocity arithmetic only and the
+    // DRAM latency hides behind the collision of the plane before.
+    const int e0 = tid - NCW * 32;
+    int sgx[SPF ? SPF : 1], sgy[SPF ? SPF : 1];
+    bool shas[SPF ? SPF : 1];
+#pragma unroll
+    for (int t = 0; t < SPF; ++t) {
+      sgx[t] = sgy[t] = 0;
+      shas[t] = slot_node(e0 + t * NFW * 32, sgx[t], sgy[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < SPF; ++t) {
+      const int e = e0 + t * NFW * 32;
+      fill(e, shas[t], sgx[t], sgy[t], m0 - 1);
+      fill(e, shas[t], sgx[t], sgy[t], m0);
+      fill(e, shas[t], sgx[t], sgy[t], m0 + 1);
+    }
+    R fv[SPF ? SPF : 1][Q];
     int mq = plane_of(m0 + 2);
-    bool okq = shas && mq >= 0;
-    if (m0 + 2 <= m1) fill_load(okq, mq, sgx, sgy, fv);
+    if (m0 + 2 <= m1) {
+#pragma unroll
+      for (int t = 0; t < SPF; ++t) fill_load(shas[t] && mq >= 0, mq, sgx[t], sgy[t], fv[t]);
+    }
     __syncthreads();
     for (int m = m0; m < m1; ++m) {
       __syncthreads();               // A: collision loads of plane m done
       if constexpr (CL) __syncthreads();  // C: learned closure done
-      if (m + 2 <= m1 && e < NE) {   // overlaps the collision of plane m
-        fill_store(e, okq, mq, sgx, sgy, fv, m + 2);
+      if (m + 2 <= m1) {             // overlaps the collision of plane m
+#pragma unroll
+        for (int t = 0; t < SPF; ++t) {
+          const int e = e0 + t * NFW * 32;
+          if (e < NE) fill_store(e, shas[t] && mq >= 0, mq, sgx[t], sgy[t], fv[t], m + 2);
+        }
         mq = plane_of(m + 3);
-        okq = shas && mq >= 0;
-        if (m + 3 <= m1) fill_load(okq, mq, sgx, sgy, fv);
+        if (m + 3 <= m1) {
+#pragma unroll
+          for (int t = 0; t < SPF; ++t) fill_load(shas[t] && mq >= 0, mq, sgx[t], sgy[t], fv[t]);
+        }
       }
       if constexpr (NBUF == 1) __syncthreads();  // B
     }
@@ -529,100 +581,107 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     return;
   }
   if (!FW) {
-    fill(tid, m0 - 1);
-    fill(tid, m0);
+    int gx = 0, gy = 0;
+    const bool has = slot_node(tid, gx, gy);
+    fill(tid, has, gx, gy, m0 - 1);
+    fill(tid, has, gx, gy, m0);
   }
 
   // ---------------- collision warps ------------------------------------------
+  // Node n < XN of this thread: x + 32 n, sAd / sPf row node + 32 n, ring
+  // slot e_own + 32 n, stage column tid + n * WC.
   const int lane = tid & 31;
   const int grp = warp / C;
   const int k = warp - grp * C;         // stress component of this thread
   const int gxi = grp % GX, gyi = grp / GX;
-  const int tx = gxi * 32 + lane;       // node of the tile
+  const int tx = gxi * 32 * XN + lane;  // node of the tile
   const int ty = gyi;
-  const int node = grp * 32 + lane;     // index into sAd / sPf
+  const int node = grp * 32 * XN + lane;
   const int x = x0 + tx;
   const int y = (D == 3) ? y0 + ty : 0;
-  const bool active = (x < nx) && (D == 2 || y < ny);
+  const bool yin = D == 2 || y < ny;
+  const bool active = (x < nx) && yin;  // node 0 (nodes n > 0 only if node 0)
+  auto active_n = [&](int n) { return x + 32 * n < nx && yin; };
   const int e_own = (D == 3) ? (ty + 1) * EX + tx + 1 : tx + 1;
   // this thread's component arrays; offsets within them are 32-bit
   // (Q * pitch < 2^32 is checked at creation)
   const S* __restrict__ hin_k = b.h_in + (long long)k * Q * P;
   S* __restrict__ hout_k = b.h_out + (long long)k * Q * P;
-  // periodic neighbour offsets along x and y (constant over the march)
-  const int ox_p = (x == nx - 1) ? -(nx - 1) : 1;
-  const int ox_m = (x == 0) ? (nx - 1) : -1;
-  const uint32_t wxp = (x == nx - 1) ? (uint32_t)(-nx) : 0u;  // wrap corrections
-  const uint32_t wxm = (x == 0) ? (uint32_t)nx : 0u;
+  // periodic neighbour offsets along y (constant over the march)
   const int oy_p = (D == 3) ? ((y == ny - 1) ? -(ny - 1) * nx : nx) : 0;
   const int oy_m = (D == 3) ? ((y == 0) ? (ny - 1) * nx : -nx) : 0;
-  // issue the copies of plane q's populations into stage buffer st
   const bool pf = PF && (!PAIR || (nx & 1) == 0);
   const unsigned amask = __ballot_sync(0xffffffffu, active);  // all 32 lanes are here
-  // Whole rows: when all 32 nodes of the warp are in the grid and a row of
-  // them starts on a 16-byte boundary (nx a multiple of 16 bytes' worth of
-  // elements; pitch and array bases are), the warp copies its rows in
-  // 16-byte chunks, spread over the lanes, instead of one element per lane.
+  // Whole rows: when all 32 nodes of a warp's row are in the grid and the row
+  // starts on a 16-byte boundary (nx a multiple of 16 bytes' worth of
+  // elements; pitch and array bases are), the warp copies it in 16-byte
+  // chunks, spread over the lanes, instead of one element per lane.
   constexpr int EPC = 16 / (int)sizeof(S);     // elements per chunk
   constexpr bool WIDE = D == 3 || sizeof(S) == 2;
-  const bool wide = PF && WIDE && amask == 0xffffffffu && (nx % EPC) == 0;
-  // Every call by a thread that stages commits exactly one group (empty
-  // past the end of the chunk), so a wait for all but the newest NST - 2
-  // groups completes plane m's copies.
+  auto wide_n = [&](int n) {
+    return PF && WIDE && yin && x0 + gxi * 32 * XN + 32 * n + 31 < nx && (nx % EPC) == 0;
+  };
+  // Issue the copies of plane q's populations of every node of this thread
+  // into stage buffer st.  Every call by a thread that stages commits exactly
+  // one group (empty past the end of the chunk), so a wait for all but the
+  // newest NST - 2 groups completes plane m's copies.
   auto prefetch = [&](int q, int st) {
     if constexpr (PF) {
       if (!pf || !active) return;
-      if (q >= m1) {
-        cp_commit();
-        return;
-      }
-      const long long sq = (D == 3) ? ((long long)q * ny + y) * nx + x : (long long)q * nx + x;
-      const uint32_t sq32 = (uint32_t)sq;
-      if (wide) {
-        constexpr int CPR = 32 / EPC;          // chunks per row of 32 nodes
-        constexpr int NCP = NPP * CPR;         // population chunks
-        constexpr int NCH = NCP + 32 * 4 / 16; // and chi (4-byte) chunks
-        const uint32_t s0 = sq32 - (uint32_t)lane;  // node of lane 0
-        const int wb = tid - lane;             // the warp's stage columns
+      if (q < m1) {
 #pragma unroll
-        for (int jj = 0; jj < (NCH + 31) / 32; ++jj) {
-          const int c = lane + 32 * jj;
-          if (c < NCP) {
-            const int v = c / CPR, sub = c % CPR;
-            const int i = v < Q ? v : k + (v - Q) * C;
-            const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + s0 + (uint32_t)(sub * EPC));
-            if (i < Q) cp_async<16>(&stage[st][v][wb + sub * EPC], src);
-          } else if (c < NCH) {
-            const int sub = c - NCP;
-            cp_async<16>(&stage_x[st][wb + sub * 4], b.chi + ((uint32_t)k * P32 + s0 + (uint32_t)(sub * 4)));
+        for (int n = 0; n < XN; ++n) {
+          if (!active_n(n)) continue;
+          const long long sq = (D == 3) ? ((long long)q * ny + y) * nx + x + 32 * n
+                                        : (long long)q * nx + x + 32 * n;
+          const uint32_t sq32 = (uint32_t)sq;
+          const int col = tid + n * WC;
+          if (wide_n(n)) {
+            constexpr int CPR = 32 / EPC;          // chunks per row of 32 nodes
+            constexpr int NCP = NPP * CPR;         // population chunks
+            constexpr int NCH = NCP + 32 * 4 / 16; // and chi (4-byte) chunks
+            const uint32_t s0 = sq32 - (uint32_t)lane;  // node of lane 0
+            const int wb = col - lane;             // the row's stage columns
+#pragma unroll
+            for (int jj = 0; jj < (NCH + 31) / 32; ++jj) {
+              const int c = lane + 32 * jj;
+              if (c < NCP) {
+                const int v = c / CPR, sub = c % CPR;
+                const int i = v < Q ? v : k + (v - Q) * C;
+                const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + s0 + (uint32_t)(sub * EPC));
+                if (i < Q) cp_async<16>(&stage[st][v][wb + sub * EPC], src);
+              } else if (c < NCH) {
+                const int sub = c - NCP;
+                cp_async<16>(&stage_x[st][wb + sub * 4], b.chi + ((uint32_t)k * P32 + s0 + (uint32_t)(sub * 4)));
+              }
+            }
+            continue;
           }
+          if constexpr (PAIR) {
+            // lanes 2j, 2j + 1 hold nodes sq, sq + 1 (x even, nx even)
+            const int par = tid & 1;
+            const int tb = col - par;
+            const uint32_t sp = sq32 - (uint32_t)par;
+#pragma unroll
+            for (int jj = 0; jj < (NPP + 1) / 2; ++jj) {
+              const int v = 2 * jj + par;
+              const int i = v < Q ? v : k + (v - Q) * C;
+              const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + sp);
+              if (v < NPP && i < Q) cp_async<4>(&stage[st][v][tb], src);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cp_async<4>(&stage[st][i][col], hin_k + ((uint32_t)i * P32 + sq32));
+#pragma unroll
+            for (int j = 0; j < NFM; ++j) {
+              const int i = k + j * C;
+              if (i < Q) cp_async<4>(&stage[st][Q + j][col], b.f_in + ((uint32_t)i * P32 + sq32));
+            }
+          }
+          static_assert(sizeof(X) == 4, "chi is staged in 4-byte copies");
+          cp_async<4>(&stage_x[st][col], b.chi + ((uint32_t)k * P32 + sq32));
         }
-        cp_commit();
-        return;
       }
-      if constexpr (PAIR) {
-        // lanes 2j, 2j + 1 hold nodes sq, sq + 1 (x even, nx even)
-        const int par = tid & 1;
-        const int tb = tid - par;
-        const uint32_t sp = sq32 - (uint32_t)par;
-#pragma unroll
-        for (int jj = 0; jj < (NPP + 1) / 2; ++jj) {
-          const int v = 2 * jj + par;
-          const int i = v < Q ? v : k + (v - Q) * C;
-          const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + sp);
-          if (v < NPP && i < Q) cp_async<4>(&stage[st][v][tb], src);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) cp_async<4>(&stage[st][i][tid], hin_k + ((uint32_t)i * P32 + sq32));
-#pragma unroll
-        for (int j = 0; j < NFM; ++j) {
-          const int i = k + j * C;
-          if (i < Q) cp_async<4>(&stage[st][Q + j][tid], b.f_in + ((uint32_t)i * P32 + sq32));
-        }
-      }
-      static_assert(sizeof(X) == 4, "chi is staged in 4-byte copies");
-      cp_async<4>(&stage_x[st][tid], b.chi + ((uint32_t)k * P32 + sq32));
       cp_commit();
     }
   };
@@ -635,9 +694,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   for (int m = m0; m < m1; ++m) {
     const int rm = slot(m - 1), rc = slot(m), rp = slot(m + 1);
     const long long s = (D == 3) ? ((long long)m * ny + y) * nx + x : (long long)m * nx + x;
-    const uint32_t s32 = (uint32_t)s;
+    const uint32_t s32 = (uint32_t)s;   // node 0; node n is s32 + 32 n
 
-    // ---- memory phase: this node's populations of component k ---------------
+    // ---- memory phase: this thread's populations of component k ---------------
     // (without fill warps, the first NE threads also load the populations of
     // their ring slot of plane m + 1)
     int fgx = 0, fgy = 0;
@@ -658,41 +717,55 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     R hv[PF ? 1 : Q], fo[PF ? 1 : NFM];
     R old = R(0);
     if (active) {
-      R a = R(0), psum = R(0);
       if constexpr (PF) {
         if (pf) {
-          // this plane's copies (issued one plane ago); then start the next.
-          // Whole-row chunks and a pair's copies were issued by other lanes
-          // too: the active lanes synchronise after the wait so that each
-          // sees the others' (both lanes of a pair are active or neither is;
-          // whole rows imply all 32 lanes).  The same synchronisation tells
-          // them that every lane has finished the collision of plane m - 1,
-          // whose buffer the next copies overwrite.
+          // this plane's copies (issued NST - 1 planes ago); then start the
+          // next.  Whole-row chunks and a pair's copies were issued by other
+          // lanes too: the active lanes synchronise after the wait so that
+          // each sees the others' (both lanes of a pair are active or
+          // neither is; whole rows imply all 32 lanes).  The same
+          // synchronisation tells them that every lane has finished the
+          // collision of plane m - 1, whose buffer (NST = 2) the next
+          // copies overwrite.
           if constexpr (NST == 3) cp_wait_group<1>();
           else cp_wait_all();
-          if (PAIR || wide) __syncwarp(amask);
+          if (PAIR || WIDE) __syncwarp(amask);
           prefetch(m + NST - 1, st_ahead);
         } else {
-          // no copies for this kernel: the node's own values into its own
-          // stage column
+          // no copies for this kernel: the nodes' own values into their own
+          // stage columns
 #pragma unroll
-          for (int i = 0; i < Q; ++i) stage[st][i][tid] = hin_k[(uint32_t)i * P32 + s32];
+          for (int n = 0; n < XN; ++n) {
+            if (!active_n(n)) continue;
+            const int col = tid + n * WC;
+            const uint32_t sn32 = s32 + 32u * n;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) stage[st][i][col] = hin_k[(uint32_t)i * P32 + sn32];
+#pragma unroll
+            for (int j = 0; j < NFM; ++j) {
+              const int i = k + j * C;
+              if (i < Q) stage[st][Q + j][col] = b.f_in[(uint32_t)i * P32 + sn32];
+            }
+            stage_x[st][col] = b.chi[(uint32_t)k * P32 + sn32];
+          }
+        }
+#pragma unroll
+        for (int n = 0; n < XN; ++n) {
+          if (!active_n(n)) continue;
+          const int col = tid + n * WC;
+          R a = R(0), psum = R(0);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) a += Store<S>::cvt(stage[st][i][col]);
 #pragma unroll
           for (int j = 0; j < NFM; ++j) {
             const int i = k + j * C;
-            if (i < Q) stage[st][Q + j][tid] = b.f_in[(uint32_t)i * P32 + s32];
+            if (i != 0 && i < Q) psum += Store<S>::cvt(stage[st][Q + j][col]);
           }
-          stage_x[st][tid] = b.chi[(uint32_t)k * P32 + s32];
+          sAd[m & (NBUF - 1)][node + 32 * n][k] = a;
+          sPf[m & (NBUF - 1)][node + 32 * n][k] = psum;
         }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) a += Store<S>::cvt(stage[st][i][tid]);
-#pragma unroll
-        for (int j = 0; j < NFM; ++j) {
-          const int i = k + j * C;
-          if (i != 0 && i < Q) psum += Store<S>::cvt(stage[st][Q + j][tid]);
-        }
-        old = R(stage_x[st][tid]);
       } else {
+        R a = R(0), psum = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) hv[i] = Store<S>::ld(hin_k + ((uint32_t)i * P32 + s32));
 #pragma unroll
@@ -708,9 +781,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           const int i = k + j * C;
           if (i != 0 && i < Q) psum += fo[j];
         }
+        sAd[m & (NBUF - 1)][node][k] = a;
+        sPf[m & (NBUF - 1)][node][k] = psum;
       }
-      sAd[m & (NBUF - 1)][node][k] = a;
-      sPf[m & (NBUF - 1)][node][k] = psum;
     }
     if constexpr (!FW) {
       if (fslot) fill_store(tid, fok, mn, fgx, fgy, fn, m + 1);
@@ -801,24 +874,31 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     }
 
     // ---- collision phase ------------------------------------------------------
-    if (active) {
+#pragma unroll 1
+    for (int n = 0; n < XN; ++n) {
+      if (!active_n(n)) break;
+      const int xn = x + 32 * n;
+      const int nd = node + 32 * n;
+      const int eo = e_own + 32 * n;
+      const int col = tid + n * WC;
+      const uint32_t sn32 = s32 + 32u * n;
       R u[D];
       {
-        const Vel<R, D> t = ring[rc][e_own];
+        const Vel<R, D> t = ring[rc][eo];
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = t.v[a];
       }
       R Ad[C];
-      lds_row<R, C>(&sAd[m & (NBUF - 1)][node][0], Ad);
+      lds_row<R, C>(&sAd[m & (NBUF - 1)][nd][0], Ad);
       R sumf = R(0);
       {
         R pf[C];
-        lds_row<R, C>(&sPf[m & (NBUF - 1)][node][0], pf);
+        lds_row<R, C>(&sPf[m & (NBUF - 1)][nd][0], pf);
 #pragma unroll
         for (int q = 0; q < C; ++q) sumf += pf[q];
       }
       R F[3];
-      body_force<L, R>(ph, x, D == 3 ? y : m, F);
+      body_force<L, R>(ph, xn, D == 3 ? y : m, F);
       R uu = R(0), Fu = R(0);
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -845,7 +925,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           Ad_k = Ad[q];
           A_k = Ad[q] + (diag<L>(q) ? R(1) : R(0));
           if constexpr (CL) {
-            chi_k = cls.chi[q][node];
+            chi_k = cls.chi[q][nd];
           } else {
             constexpr int a = L::ca(q), bb = L::cb(q);
             R v = -Ad[q] * ph.inv_lam;
@@ -857,13 +937,13 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                 int e_p, e_m, r_p, r_m;
                 bool lo, hi;
                 if (r == 0) {
-                  e_p = e_own + 1; e_m = e_own - 1; r_p = rc; r_m = rc;
-                  lo = wall_x && x == 0; hi = wall_x && x == nx - 1;
+                  e_p = eo + 1; e_m = eo - 1; r_p = rc; r_m = rc;
+                  lo = wall_x && xn == 0; hi = wall_x && xn == nx - 1;
                 } else if (r == 1 && D == 3) {
-                  e_p = e_own + EX; e_m = e_own - EX; r_p = rc; r_m = rc;
+                  e_p = eo + EX; e_m = eo - EX; r_p = rc; r_m = rc;
                   lo = wall_y && y == 0; hi = wall_y && y == ny - 1;
                 } else {
-                  e_p = e_own; e_m = e_own; r_p = rp; r_m = rm;
+                  e_p = eo; e_m = eo; r_p = rp; r_m = rm;
                   lo = wall_m && m == 0; hi = wall_m && m == nm - 1;
                 }
                 const Vel<R, D> vp = ring[r_p][e_p], vm = ring[r_m][e_m];
@@ -882,26 +962,32 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           }
         }
       });
-      if (ph.first) old = chi_k;
-      b.chi[(uint32_t)k * P32 + s32] = X(chi_k);
-      const R src = R(1.5) * chi_k - R(0.5) * old;
+      R oldn = old;
+      if constexpr (PF) oldn = R(stage_x[st][col]);
+      if (ph.first) oldn = chi_k;
+      b.chi[(uint32_t)k * P32 + sn32] = X(chi_k);
+      const R src = R(1.5) * chi_k - R(0.5) * oldn;
       uint32_t rng = Store<S>::sr
-                         ? hash32(((uint32_t)s * 8u + (uint32_t)k) * 0x9e3779b9u ^ hash32(ph.step))
+                         ? hash32((sn32 * 8u + (uint32_t)k) * 0x9e3779b9u ^ hash32(ph.step))
                          : 0u;
 
-      // neighbour offsets along the march axis (periodic wrap)
+      // neighbour offsets along x (this node) and the march axis (periodic wrap)
+      const int ox_p = (xn == nx - 1) ? -(nx - 1) : 1;
+      const int ox_m = (xn == 0) ? (nx - 1) : -1;
+      const uint32_t wxp = (xn == nx - 1) ? (uint32_t)(-nx) : 0u;  // wrap corrections
+      const uint32_t wxm = (xn == 0) ? (uint32_t)nx : 0u;
       const int strm = (D == 3) ? nx * ny : nx;
       const int om_p = (m == nm - 1) ? -(nm - 1) * strm : strm;
       const int om_m = (m == 0) ? (nm - 1) * strm : -strm;
       const int opos[3] = {ox_p, D == 3 ? oy_p : om_p, om_p};
       const int oneg[3] = {ox_m, D == 3 ? oy_m : om_m, om_m};
-      const int posv[3] = {x, D == 3 ? y : m, m};
+      const int posv[3] = {xn, D == 3 ? y : m, m};
       const int extv[3] = {nx, D == 3 ? ny : nm, nm};
       // destination of direction i (32-bit offset within a population
       // array): the neighbour, or the own node through a halfway-bounce-back
       // wall (direction reversed)
       auto dest = [&](int i, int& j) -> uint32_t {
-        int d = (int)s32;
+        int d = (int)sn32;
         bool bb = false;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -916,7 +1002,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         }
         if (WALLS && bb) {
           j = L::opp(i);
-          return s32;
+          return sn32;
         }
         j = i;
         return (uint32_t)d;
@@ -940,7 +1026,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if constexpr (FAST) {
             const int cx = L::cx(i);
             const uint32_t xw = cx == 1 ? wxp : (cx == -1 ? wxm : 0u);
-            return s32 + (uint32_t)i * P32 + (uint32_t)(cx + L::cy(i) * nx + L::cz(i) * strm) + xw;
+            return sn32 + (uint32_t)i * P32 + (uint32_t)(cx + L::cy(i) * nx + L::cz(i) * strm) + xw;
           } else {
             int j;
             const uint32_t d = dest(i, j);
@@ -957,7 +1043,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
             if (c == -1) cu -= u[a];
           }
           R hvi;
-          if constexpr (PF) hvi = Store<S>::cvt(stage[st][i][tid]);
+          if constexpr (PF) hvi = Store<S>::cvt(stage[st][i][col]);
           else hvi = hv[i];
           const R wa = R(L::w(i)) * alpha, wb = R(L::w(i)) * beta;
           const R post = keep * hvi + (wa + cu * wb);
@@ -985,7 +1071,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
               const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
               const R fBi = fB_dir<L, R>(i, Ad, kB);
               R foi;
-              if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][tid]);
+              if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][col]);
               else foi = fo[jj];
               const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
               Store<S>::st(b.f_out + index(i), post, Store<S>::sr ? lcg_next(rng) : 0u);
@@ -1003,10 +1089,11 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   if constexpr (NBUF == 2) __syncthreads();  // tile done (shared memory reuse)
 }
 
-template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL = false>
-__global__ void __launch_bounds__(FusedShape<L, GX, TY, FW>::NT, MINB)
+template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL = false,
+          int XN = 1>
+__global__ void __launch_bounds__(FusedShape<L, GX, TY, FW, XN>::NT, MINB)
     k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
-  fused_tile<L, S, GX, TY, WALLS, FW, CL>(g, ph, b, mchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+  fused_tile<L, S, GX, TY, WALLS, FW, CL, XN>(g, ph, b, mchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------

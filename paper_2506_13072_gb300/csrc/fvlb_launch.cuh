@@ -58,10 +58,27 @@ inline int grid_stride_blocks(long long N, int threads, int sms) {
   return (int)std::max<long long>(1, std::min(want, cap));
 }
 
-template <class L, class S, int GX, int TY, int MINB, bool FW>
+// Launch a fused-step kernel instance; a tile of more than 48 KB of shared
+// memory (XN > 1) is given it dynamically.
+template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL, int XN>
+cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
+                          const Bufs<S>& b, int mchunk) {
+  constexpr int NT = FusedShape<L, GX, TY, FW, XN>::NT;
+  constexpr size_t dyn = TileCfg<L, S, GX, TY, FW, CL, XN>::kDynamicBytes;
+  auto kern = k_step_fused<L, S, GX, TY, MINB, WALLS, FW, CL, XN>;
+  if constexpr (dyn > 0) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, NT, dyn, d.stream>>>(g, ph, b, mchunk);
+  return cudaGetLastError();
+}
+
+template <class L, class S, int GX, int TY, int MINB, bool FW, int XN = 1>
 cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                          const Bufs<S>& b) {
-  constexpr int TXS = GX * 32;
+  constexpr int TXS = GX * 32 * XN;
   const int bx = (d.nx + TXS - 1) / TXS;
   const int by = L::D == 3 ? (d.ny + TY - 1) / TY : 1;
   const int nm = L::D == 3 ? g.nz : d.ny;
@@ -75,21 +92,14 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   mchunk = std::min(mchunk, nm);
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
-  constexpr int NT = FusedShape<L, GX, TY, FW>::NT;
-  if constexpr (std::is_same<S, float>::value) {
+  if constexpr (std::is_same<S, float>::value && XN == 1) {
     if (d.mlp) {  // learned closure (FP32 storage only); one block per SM
-      if (d.walls)
-        k_step_fused<L, S, GX, TY, 1, true, FW, true><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
-      else
-        k_step_fused<L, S, GX, TY, 1, false, FW, true><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
-      return cudaGetLastError();
+      if (d.walls) return launch_kernel<L, S, GX, TY, 1, true, FW, true, 1>(grid, d, g, ph, b, mchunk);
+      return launch_kernel<L, S, GX, TY, 1, false, FW, true, 1>(grid, d, g, ph, b, mchunk);
     }
   }
-  if (d.walls)
-    k_step_fused<L, S, GX, TY, MINB, true, FW><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
-  else
-    k_step_fused<L, S, GX, TY, MINB, false, FW><<<grid, NT, 0, d.stream>>>(g, ph, b, mchunk);
-  return cudaGetLastError();
+  if (d.walls) return launch_kernel<L, S, GX, TY, MINB, true, FW, false, XN>(grid, d, g, ph, b, mchunk);
+  return launch_kernel<L, S, GX, TY, MINB, false, FW, false, XN>(grid, d, g, ph, b, mchunk);
 }
 
 template <class L, class S>
@@ -103,18 +113,24 @@ cudaError_t step_impl(const StepDesc& d) {
             static_cast<X*>(d.chi)};
   if (d.variant == 0) {
     // Shapes measured fastest on GB300 (256^3 D3Q19, 2048^2 D2Q9): 2D four
-    // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D one
-    // 32-node row x 6 components + 4 halo fill warps (320 threads, 2 blocks
-    // per SM; a 64-register cap for 3 blocks per SM measured slower).
+    // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D FP32
+    // a 64-node row, each of the 6 component warps taking its two 32-node
+    // halves in turn, + 4 halo fill warps (320 threads, 2 blocks per SM; a
+    // 64-register cap for 3 blocks per SM measured slower); 3D 16-bit, FP64
+    // and the learned closure one 32-node row.
     constexpr bool wide = sizeof(RT<S>) == 8;
     if constexpr (L::D == 2) {
       // 4 groups x 3 components, ring filled by the collision threads
       if constexpr (wide) return launch_fused<L, S, 4, 1, 1, false>(d, g, ph, b);
       else return launch_fused<L, S, 4, 1, 2, false>(d, g, ph, b);
     } else {
-      // 32 x 1 nodes x 6 components + 4 fill warps, two blocks per SM
       if constexpr (wide) return launch_fused<L, S, 1, 1, 1, true>(d, g, ph, b);
-      else return launch_fused<L, S, 1, 1, 2, true>(d, g, ph, b);
+      else if constexpr (sizeof(S) == 4) {
+        if (d.mlp) return launch_fused<L, S, 1, 1, 2, true, 1>(d, g, ph, b);
+        return launch_fused<L, S, 1, 1, 2, true, 2>(d, g, ph, b);
+      } else {
+        return launch_fused<L, S, 1, 1, 2, true, 1>(d, g, ph, b);
+      }
     }
   } else {
     const int threads = 128;
