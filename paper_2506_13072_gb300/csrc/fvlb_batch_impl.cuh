@@ -14,20 +14,32 @@ struct BatchMinB {
   static constexpr int value = GX == 4 ? 2 : (GX == 2 ? 4 : 8);
 };
 
+// dynamic shared memory of the batched kernel's tile (0: static)
+template <class S, int GX>
+constexpr size_t batch_dyn() {
+  return TileCfg<D2Q9, S, GX, 1, false, false, 1>::kDynamicBytes;
+}
+
 template <class S, int GX>
 cudaError_t batch_launch_gx(const BatchLaunch& d) {
   constexpr int MINB = BatchMinB<GX>::value;
   constexpr int NT = FusedShape<D2Q9, GX, 1, false>::NT;
+  constexpr size_t dyn = batch_dyn<S, GX>();
   using X = typename Store<S>::X;
+  auto kern = k_step_batched<D2Q9, S, GX, MINB>;
+  if constexpr (dyn > 0) {
+    const cudaError_t e = allow_dynamic_smem(kern, dyn);
+    if (e != cudaSuccess) return e;
+  }
   int blocks = d.blocks;
   if (blocks <= 0) {
     int dev = 0, sms = 1, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_batched<D2Q9, S, GX, MINB>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, dyn);
     blocks = sms * (per > 0 ? per : 1);
   }
-  k_step_batched<D2Q9, S, GX, MINB><<<blocks, NT, 0, d.stream>>>(
+  kern<<<blocks, NT, dyn, d.stream>>>(
       static_cast<const BatchInst<S>*>(d.inst), static_cast<const BatchTile*>(d.tiles),
       d.ntiles, static_cast<S*>(d.fA), static_cast<S*>(d.fB), static_cast<S*>(d.hA),
       static_cast<S*>(d.hB), static_cast<X*>(d.chi), d.parity, d.first, d.tstep, d.mchunk);
@@ -44,24 +56,25 @@ cudaError_t batch_step_impl(const BatchLaunch& d) {
   }
 }
 
+template <class S, int GX>
+int batch_occupancy_gx() {
+  auto kern = k_step_batched<D2Q9, S, GX, BatchMinB<GX>::value>;
+  constexpr size_t dyn = batch_dyn<S, GX>();
+  if constexpr (dyn > 0) {
+    if (allow_dynamic_smem(kern, dyn) != cudaSuccess) return 0;
+  }
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FusedShape<D2Q9, GX, 1, false>::NT, dyn);
+  return per;
+}
+
 template <class S>
 int batch_occupancy_impl(int gx) {
-  int per = 0;
   switch (gx) {
-    case 1:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per, k_step_batched<D2Q9, S, 1, BatchMinB<1>::value>, FusedShape<D2Q9, 1, 1, false>::NT, 0);
-      break;
-    case 2:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per, k_step_batched<D2Q9, S, 2, BatchMinB<2>::value>, FusedShape<D2Q9, 2, 1, false>::NT, 0);
-      break;
-    default:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per, k_step_batched<D2Q9, S, 4, BatchMinB<4>::value>, FusedShape<D2Q9, 4, 1, false>::NT, 0);
-      break;
+    case 1: return batch_occupancy_gx<S, 1>();
+    case 2: return batch_occupancy_gx<S, 2>();
+    default: return batch_occupancy_gx<S, 4>();
   }
-  return per;
 }
 
 template <class S>

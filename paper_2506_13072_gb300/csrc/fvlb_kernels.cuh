@@ -393,7 +393,10 @@ struct TileCfg {
   static constexpr size_t kRing = sizeof(Vel<R, D>) * 4 * Sh::NE;
   static constexpr size_t kStage1 = PF ? sizeof(S) * NPP * NCT + sizeof(X) * NCT : 0;
   static constexpr size_t kEx1 = 2 * sizeof(R) * CP * NS;
-  static constexpr bool kDynamic = XN > 1;
+  // dynamic shared memory: several rows per thread, or a staged 2D tile
+  // (whose stage fills the static 48 KB and leaves no room for the
+  // double-buffered exchange or a third stage)
+  static constexpr bool kDynamic = XN > 1 || (PF && D == 2);
   static constexpr size_t kLimit = kDynamic ? 110 * 1024 : 48 * 1024;
   static constexpr int NST =
       (PF && kRing + sizeof(CLS) + 3 * kStage1 + 2 * kEx1 <= kLimit) ? 3 : 2;

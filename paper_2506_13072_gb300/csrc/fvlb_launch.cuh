@@ -3,6 +3,9 @@
 #pragma once
 
 #include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
 #include <cstdlib>
 #include <type_traits>
 
@@ -58,6 +61,25 @@ inline int grid_stride_blocks(long long N, int threads, int sms) {
   return (int)std::max<long long>(1, std::min(want, cap));
 }
 
+// Let kernel `kern` take `bytes` of dynamic shared memory on the current
+// device: set once per device and kernel (before its first launch, so also
+// before a stream capture that contains one).
+template <class K>
+cudaError_t allow_dynamic_smem(K* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;  // (kernel, device) set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const std::pair<const void*, int> key{reinterpret_cast<const void*>(kern), dev};
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& d : done)
+    if (d == key) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.push_back(key);
+  return e;
+}
+
 // Launch a fused-step kernel instance; a tile of more than 48 KB of shared
 // memory (XN > 1) is given it dynamically.
 template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL, int XN>
@@ -67,8 +89,7 @@ cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phy
   constexpr size_t dyn = TileCfg<L, S, GX, TY, FW, CL, XN>::kDynamicBytes;
   auto kern = k_step_fused<L, S, GX, TY, MINB, WALLS, FW, CL, XN>;
   if constexpr (dyn > 0) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    const cudaError_t e = allow_dynamic_smem(kern, dyn);
     if (e != cudaSuccess) return e;
   }
   kern<<<grid, NT, dyn, d.stream>>>(g, ph, b, mchunk);
