@@ -30,6 +30,11 @@ FIELD_P = 1
 FIELD_A = 2
 FIELD_TAU_P = 3
 
+# scheme: the present method (f^B) or the original one it is compared with
+# (div tau_p as a body force, reading R8 of fvlb_oracle.c)
+SCHEME_PRESENT = 0
+SCHEME_ORIGINAL = 1
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fvlb_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
@@ -69,6 +74,8 @@ def lib():
             L.orc_set_walls.argtypes = [ctypes.c_void_p, ctypes.c_uint]
             L.orc_set_walls.restype = ctypes.c_int
             L.orc_set_tau_h.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.orc_set_scheme.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_set_scheme.restype = ctypes.c_int
             L.orc_time.argtypes = [ctypes.c_void_p]
             L.orc_time.restype = ctypes.c_long
             L.orc_init.argtypes = [ctypes.c_void_p, dp, dp, dp]
@@ -184,7 +191,7 @@ class Oracle:
 
     def __init__(self, lat, nx, ny, nz=1, tau_s=0.8, eta_p=0.0, lam=1.0,
                  force_kind=FORCE_NONE, F0=(0.0, 0.0, 0.0), k=0.0, omega=0.0,
-                 walls=0, tau_h=None):
+                 walls=0, tau_h=None, scheme=SCHEME_PRESENT):
         self.lat = lat
         self.D = 2 if lat == D2Q9 else 3
         self.Q = qsize(lat)
@@ -198,6 +205,10 @@ class Oracle:
                                    float(omega))
         if not self._h:
             raise ValueError("invalid oracle parameters")
+        if lib().orc_set_scheme(self._h, int(scheme)) != 0:
+            lib().orc_destroy(self._h)
+            self._h = None
+            raise ValueError("invalid scheme")
         if lib().orc_set_walls(self._h, int(walls)) != 0:
             lib().orc_destroy(self._h)
             self._h = None

@@ -32,6 +32,16 @@
  *   R5  Walls are halfway bounce-back for both f and h.
  *   R6  The body force is evaluated at the time level of the step, t_n = n.
  *   R7  Initial state: f = f^eq(p0, u0), h = h^eq(A0, u0).
+ *   R8  The "original" scheme the paper compares against (Sec. 1, Tables 1
+ *       and 2) adds the polymer stress divergence to the momentum equation
+ *       as a body force instead of the fluctuation term: f^B = 0 and
+ *       F -> F + div tau_p, with tau_p from A of the same step and
+ *       (div tau_p)_b = sum_a d_a tau_ab by second-order central
+ *       differences (periodic wrap); at a node next to a wall the
+ *       second-order one-sided difference through the two nodes inside,
+ *       (-3 t0 + 4 t1 - t2) / 2 (sign mirrored at the upper wall), since no
+ *       stress is known at the wall.  The total force enters u, the Guo
+ *       term and the pressure as the body force does in the present scheme.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -243,6 +253,8 @@ typedef struct orc {
   double *chi_old;   /* [N][DD] */
   double *u;         /* [N][3] velocity of the current step */
   double *A;         /* [N][DD] conformation of the current step */
+  int scheme;        /* 0: present (f^B), 1: original (div tau_p as a force) */
+  double *divt;      /* [N][3] div tau_p of the current step (scheme 1) */
   int first;
   long t;
 } orc;
@@ -307,10 +319,11 @@ orc *orc_create(int lattice, int nx, int ny, int nz, double tau_s,
   o->chi_old = (double *)calloc((size_t)N * o->DD, sizeof(double));
   o->u = (double *)calloc((size_t)N * 3, sizeof(double));
   o->A = (double *)calloc((size_t)N * o->DD, sizeof(double));
+  o->divt = (double *)calloc((size_t)N * 3, sizeof(double));
   if (!o->f || !o->f_new || !o->h || !o->h_new || !o->chi_old || !o->u ||
-      !o->A) {
+      !o->A || !o->divt) {
     free(o->f); free(o->f_new); free(o->h); free(o->h_new);
-    free(o->chi_old); free(o->u); free(o->A); free(o);
+    free(o->chi_old); free(o->u); free(o->A); free(o->divt); free(o);
     return NULL;
   }
   o->first = 1;
@@ -320,15 +333,26 @@ orc *orc_create(int lattice, int nx, int ny, int nz, double tau_s,
 void orc_destroy(orc *o) {
   if (!o) return;
   free(o->f); free(o->f_new); free(o->h); free(o->h_new);
-  free(o->chi_old); free(o->u); free(o->A); free(o);
+  free(o->chi_old); free(o->u); free(o->A); free(o->divt); free(o);
 }
 
 int orc_set_walls(orc *o, unsigned mask) {
   for (int a = 0; a < 3; ++a) {
     const int on = (mask >> a) & 1u;
-    if (on && (a >= o->D || o->n[a] < 2)) return -1;
-    o->walls[a] = on;
+    if (on && (a >= o->D || o->n[a] < (o->scheme ? 3 : 2))) return -1;
   }
+  for (int a = 0; a < 3; ++a) o->walls[a] = (mask >> a) & 1u;
+  return 0;
+}
+
+/* Scheme 0: the present method (Sec. 2.2, f^B); scheme 1: the original one
+ * (reading R8), which needs 3 nodes across a walled axis. */
+int orc_set_scheme(orc *o, int scheme) {
+  if (scheme != 0 && scheme != 1) return -1;
+  if (scheme == 1)
+    for (int a = 0; a < 3; ++a)
+      if (o->walls[a] && o->n[a] < 3) return -1;
+  o->scheme = scheme;
   return 0;
 }
 
@@ -359,25 +383,76 @@ void orc_init(orc *o, const double *u0, const double *p0, const double *A0) {
   o->t = 0;
 }
 
-/* Velocity (Sec. 2.2, u = sum_{i!=0} c_i f_i + F/2) and conformation
- * (Sec. 2.3, A_ab = sum_i h_ab,i) of every site, at the current time. */
+/* (eta_p / lambda)(A - I)_{ab} at site s (Sec. 2.1) */
+static double tau_p_at(const orc *o, long s, int a, int b) {
+  return o->eta_p / o->lambda * (o->A[s * o->DD + T(o->D, a, b)] - (a == b ? 1.0 : 0.0));
+}
+
+/* d_a tau_ab at node p (reading R8). */
+static double dtau(const orc *o, const int p[3], int a, int b) {
+  const int n = o->n[a];
+  int q[3] = {p[0], p[1], p[2]};
+  if (n == 1) return 0.0;
+  if (o->walls[a] && (p[a] == 0 || p[a] == n - 1)) {
+    const int dir = p[a] == 0 ? 1 : -1;
+    const double t0 = tau_p_at(o, site_index(o, p[0], p[1], p[2]), a, b);
+    q[a] = p[a] + dir;
+    const double t1 = tau_p_at(o, site_index(o, q[0], q[1], q[2]), a, b);
+    q[a] = p[a] + 2 * dir;
+    const double t2 = tau_p_at(o, site_index(o, q[0], q[1], q[2]), a, b);
+    return dir * 0.5 * (-3.0 * t0 + 4.0 * t1 - t2);
+  }
+  q[a] = (p[a] + 1) % n;
+  const double tp = tau_p_at(o, site_index(o, q[0], q[1], q[2]), a, b);
+  q[a] = (p[a] - 1 + n) % n;
+  const double tm = tau_p_at(o, site_index(o, q[0], q[1], q[2]), a, b);
+  return 0.5 * (tp - tm);
+}
+
+/* Body force of the step at a site: the external force, plus div tau_p in
+ * the original scheme. */
+static void total_force(const orc *o, int x, int y, int z, double F[3]) {
+  force_at(o, x, y, z, o->t, F);
+  if (o->scheme) {
+    const long s = site_index(o, x, y, z);
+    for (int b = 0; b < 3; ++b) F[b] += o->divt[s * 3 + b];
+  }
+}
+
+/* Conformation (Sec. 2.3, A_ab = sum_i h_ab,i), in the original scheme the
+ * stress divergence (reading R8), and velocity (Sec. 2.2,
+ * u = sum_{i!=0} c_i f_i + F/2) of every site, at the current time. */
 static void moments_sweep(orc *o) {
+  for (long s = 0; s < o->N; ++s)
+    for (int ab = 0; ab < o->DD; ++ab) {
+      double m = 0.0;
+      for (int i = 0; i < o->Q; ++i) m += o->h[(s * o->DD + ab) * o->Q + i];
+      o->A[s * o->DD + ab] = m;
+    }
+  if (o->scheme)
+    for (int z = 0; z < o->n[2]; ++z)
+      for (int y = 0; y < o->n[1]; ++y)
+        for (int x = 0; x < o->n[0]; ++x) {
+          const int p[3] = {x, y, z};
+          const long s = site_index(o, x, y, z);
+          for (int b = 0; b < 3; ++b) {
+            double d = 0.0;
+            if (b < o->D)
+              for (int a = 0; a < o->D; ++a) d += dtau(o, p, a, b);
+            o->divt[s * 3 + b] = d;
+          }
+        }
   for (int z = 0; z < o->n[2]; ++z)
     for (int y = 0; y < o->n[1]; ++y)
       for (int x = 0; x < o->n[0]; ++x) {
         const long s = site_index(o, x, y, z);
         const double *f = &o->f[s * o->Q];
         double F[3];
-        force_at(o, x, y, z, o->t, F);
+        total_force(o, x, y, z, F);
         for (int a = 0; a < 3; ++a) {
           double m = 0.0;
           for (int i = 1; i < o->Q; ++i) m += o->L.c[i][a] * f[i];
           o->u[s * 3 + a] = m + 0.5 * F[a];
-        }
-        for (int ab = 0; ab < o->DD; ++ab) {
-          double m = 0.0;
-          for (int i = 0; i < o->Q; ++i) m += o->h[(s * o->DD + ab) * o->Q + i];
-          o->A[s * o->DD + ab] = m;
         }
       }
 }
@@ -450,7 +525,7 @@ static void step_once(orc *o) {
         const double *A = &o->A[s * DD];
         const double *u = &o->u[s * 3];
         double F[3];
-        force_at(o, x, y, z, o->t, F);
+        total_force(o, x, y, z, F);
 
         /* tau_p = (eta_p / lambda)(A - I), Sec. 2.1 */
         for (int a = 0; a < D; ++a)
@@ -459,6 +534,8 @@ static void step_once(orc *o) {
                 o->eta_p / o->lambda * (A[T(D, a, b)] - (a == b ? 1.0 : 0.0));
 
         fB_site(L, o->tau_f, tau_p, fB);
+        if (o->scheme)
+          for (int i = 0; i < Q; ++i) fB[i] = 0.0;  /* reading R8 */
         forcing_site(L, o->tau_f, F, u, Fi);
         const double pr = pressure_site(L, o->tau_f, f, u, Fi[0], fB[0]);
         feq_site(L, pr, u, feq);
@@ -538,8 +615,10 @@ int orc_fields(orc *o, int which, double *out) {
             break;
           case ORC_FIELD_P: {
             double F[3];
-            force_at(o, x, y, z, o->t, F);
+            total_force(o, x, y, z, F);
             fB_site(L, o->tau_f, tau_p, fB);
+            if (o->scheme)
+              for (int i = 0; i < Q; ++i) fB[i] = 0.0;
             forcing_site(L, o->tau_f, F, u, Fi);
             out[s] = pressure_site(L, o->tau_f, &o->f[s * Q], u, Fi[0], fB[0]);
             break;

@@ -17,8 +17,13 @@ CS2 = 1.0 / 3.0
 
 
 class NumpyLB:
-    def __init__(self, pr):
+    """scheme 0: the present method; 1: the original one (div tau_p as a body
+    force, no f^B), the divergence by np.roll central differences with the
+    two wall rows replaced by one-sided second-order differences."""
+
+    def __init__(self, pr, scheme=0):
         self.pr = pr
+        self.scheme = scheme
         self.D = pr.D
         c, w, opp = O.lattice(pr.lattice)   # lattice tables are pinned separately
         self.c = c[:, : self.D].astype(float)
@@ -95,6 +100,30 @@ class NumpyLB:
             g[..., a, :] = d
         return g
 
+    def div(self, tau):
+        """d[..., b] = sum_a d_a tau[..., a, b]."""
+        D = self.D
+        d = np.zeros(self.shape + (D,))
+        for a in range(D):
+            ax = self.axis(a)
+            n = self.shape[ax]
+            if n == 1:
+                continue
+            t = tau[..., a, :]
+            g = 0.5 * (np.roll(t, -1, axis=ax) - np.roll(t, 1, axis=ax))
+            if (self.pr.walls >> a) & 1:
+                def row(j):
+                    return np.take(t, j, axis=ax)
+                lo = 0.5 * (-3 * row(0) + 4 * row(1) - row(2))
+                hi = -0.5 * (-3 * row(n - 1) + 4 * row(n - 2) - row(n - 3))
+                idx = [slice(None)] * (len(self.shape) + 1)
+                idx[ax] = 0
+                g[tuple(idx)] = lo
+                idx[ax] = n - 1
+                g[tuple(idx)] = hi
+            d += g
+        return d
+
     def stream(self, post):
         """post[..., i] -> populations after streaming with wrap / bounce-back."""
         out = np.zeros_like(post)
@@ -125,12 +154,16 @@ class NumpyLB:
         I = np.eye(D)
         F = self.force(self.t)
         f, h = self.f, self.h
-        u = np.einsum("...i,ia->...a", f, c) + 0.5 * F
         A = h.sum(axis=-1)
         tau_p = pr.eta_p / pr.lam * (A - I)
+        if self.scheme:
+            F = F + self.div(tau_p)
+        u = np.einsum("...i,ia->...a", f, c) + 0.5 * F
         b = np.concatenate([np.zeros(self.shape + (1 + D,)),
                             (-tau_p / pr.tau_s).reshape(self.shape + (D * D,))], axis=-1)
         fB = np.einsum("iq,...q->...i", self.P, b)
+        if self.scheme:
+            fB = np.zeros_like(fB)
         Qt = np.einsum("ia,ib->iab", c, c) - CS2 * I
         Fu = np.einsum("...a,...b->...ab", F, u)
         Fi = w * (1 - 0.5 / pr.tau_s) * (np.einsum("ia,...a->...i", c, F) / CS2
@@ -161,14 +194,17 @@ class NumpyLB:
 
     def fields(self):
         F = self.force(self.t)
+        A = self.h.sum(-1)
+        if self.scheme:
+            F = F + self.div(self.pr.eta_p / self.pr.lam * (A - np.eye(self.D)))
         u = np.einsum("...i,ia->...a", self.f, self.c) + 0.5 * F
-        return u, self.h.sum(-1)
+        return u, A
 
 
-def _compare(pr, steps):
-    o = O.Oracle(pr.lattice, **pr.oracle_kwargs())
+def _compare(pr, steps, scheme=0):
+    o = O.Oracle(pr.lattice, scheme=scheme, **pr.oracle_kwargs())
     o.init(u=pr.u0, p=pr.p0, A=pr.A0)
-    nb = NumpyLB(pr)
+    nb = NumpyLB(pr, scheme)
     nb.init(pr.u0, pr.p0, pr.A0)
     for _ in range(steps):
         nb.step()
