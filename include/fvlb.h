@@ -97,6 +97,12 @@ enum {
  * step (velocity field to a device buffer, then collide-and-stream). */
 enum { FVLB_KERNEL_FUSED = 0, FVLB_KERNEL_SPLIT = 1 };
 
+/* Scheme: PRESENT is the paper's method (the polymer stress enters the flow
+ * through the fluctuation term f^B, Sec. 2.2); ORIGINAL is the conventional
+ * scheme the paper compares it with (Sec. 1, Tables 1 and 2): no f^B, the
+ * stress divergence added to the body force. */
+enum { FVLB_SCHEME_PRESENT = 0, FVLB_SCHEME_ORIGINAL = 1 };
+
 /* Fields for fvlb_fields. */
 enum {
   FVLB_FIELD_U = 0,    /* u = sum_{i!=0} c_i f_i + F/2 (Sec. 2.2)            */
@@ -146,6 +152,21 @@ int fvlb_set_precision(fvlb_t h, int storage);
 /* Kernel variant (FVLB_KERNEL_FUSED or FVLB_KERNEL_SPLIT); may be changed
  * at any time, both give the same results up to rounding order. */
 int fvlb_set_kernel(fvlb_t h, int variant);
+
+/* Scheme (FVLB_SCHEME_PRESENT, the default, or FVLB_SCHEME_ORIGINAL); may be
+ * changed between steps.  The original scheme (Sec. 1; the comparison of
+ * Tables 1 and 2) keeps the stress LB of Sec. 2.3 and replaces f^B by the
+ * body force div tau_p: the polymer stress of every node goes to a working
+ * array of C x pitch values (allocated through the allocator hooks at the
+ * first step, field or reduction that needs it), its divergence is taken by
+ * central differences (periodic wrap) and, next to a wall, by the one-sided
+ * second-order difference through the two nodes inside, and it enters the
+ * velocity, the Guo forcing term and the pressure as the body force does.
+ * It runs as three launches per step (stress, velocity, collide-and-stream)
+ * whatever the kernel variant; fvlb_fields and fvlb_reduce use the same
+ * total force.  FVLB_EINVAL for an unknown scheme, for a walled axis of
+ * fewer than 3 nodes, or while a learned closure is attached. */
+int fvlb_set_scheme(fvlb_t h, int scheme);
 
 /* CUDA stream (a cudaStream_t, or NULL for the legacy default stream) on
  * which all later GPU work of the handle is enqueued. */

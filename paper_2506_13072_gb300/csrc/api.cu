@@ -69,6 +69,8 @@ struct fvlb_s {
   fvlb_mlp_t mlp = nullptr; // learned closure, or null
   double cl_tol = 1e-2;
   unsigned long long* cl_count = nullptr;  // [0] network nodes, [1] fallbacks
+  int scheme = FVLB_SCHEME_PRESENT;
+  void* taup = nullptr;     // original scheme: polymer stress working array
   fvlb_alloc_fn alloc = nullptr;
   fvlb_free_fn free_ = nullptr;
   void* actx = nullptr;
@@ -117,6 +119,7 @@ void free_all(fvlb_t h) {
   h->chi = h->ubuf = h->tables = nullptr;
   h->part = h->red = h->fbuf = nullptr;
   h->cl_count = nullptr;
+  h->taup = nullptr;
   h->allocated = false;
 }
 
@@ -150,6 +153,8 @@ StepDesc make_desc(fvlb_t h) {
   d.mlp = h->mlp ? fvlb::mlp_packed(h->mlp) : nullptr;
   d.cl_tol = h->cl_tol;
   d.cl_count = h->cl_count;
+  d.scheme = h->scheme;
+  d.taup = h->taup;
   double c = 0.0;
   if (h->force.kind == FVLB_FORCE_CONST) c = 1.0;
   if (h->force.kind == FVLB_FORCE_COSINE) c = std::cos(h->force.omega * (double)h->t);
@@ -397,9 +402,27 @@ int fvlb_set_walls(fvlb_t h, unsigned mask) {
   const int n[3] = {h->nx, h->ny, h->nz};
   if (mask >> h->D) return fail(h, FVLB_EINVAL, "fvlb_set_walls: wall on a missing axis");
   for (int a = 0; a < h->D; ++a)
-    if (((mask >> a) & 1u) && n[a] < 2)
-      return fail(h, FVLB_EINVAL, "fvlb_set_walls: a walled axis needs >= 2 nodes");
+    if (((mask >> a) & 1u) && n[a] < (h->scheme == FVLB_SCHEME_ORIGINAL ? 3 : 2))
+      return fail(h, FVLB_EINVAL,
+                  "fvlb_set_walls: a walled axis needs >= 2 nodes (>= 3 with the original scheme)");
   h->walls = mask;
+  return FVLB_OK;
+}
+
+int fvlb_set_scheme(fvlb_t h, int scheme) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  if (scheme != FVLB_SCHEME_PRESENT && scheme != FVLB_SCHEME_ORIGINAL)
+    return fail(h, FVLB_EINVAL, "fvlb_set_scheme: unknown scheme");
+  if (scheme == FVLB_SCHEME_ORIGINAL) {
+    const int n[3] = {h->nx, h->ny, h->nz};
+    for (int a = 0; a < h->D; ++a)
+      if (((h->walls >> a) & 1u) && n[a] < 3)
+        return fail(h, FVLB_EINVAL,
+                    "fvlb_set_scheme: the original scheme needs >= 3 nodes across a wall");
+    if (h->mlp)
+      return fail(h, FVLB_EINVAL, "fvlb_set_scheme: a learned closure is attached");
+  }
+  h->scheme = scheme;
   return FVLB_OK;
 }
 
@@ -435,10 +458,22 @@ int fvlb_init_fields(fvlb_t h, const double* u0, const double* p0, const double*
   return run_init(h, u0, p0, A0);
 }
 
+// the original scheme's polymer stress array (C * pitch working-precision
+// values), allocated on first need through the allocator hooks
+int ensure_taup(fvlb_t h) {
+  if (h->scheme != FVLB_SCHEME_ORIGINAL || h->taup) return FVLB_OK;
+  const size_t rb = h->storage == FVLB_FP64 ? 8 : 4;
+  h->taup = dev_alloc(h, rb * (size_t)h->C * (size_t)h->pitch);
+  if (!h->taup) return fail(h, FVLB_ENOMEM, "device allocation of the stress array failed");
+  return FVLB_OK;
+}
+
 int fvlb_step(fvlb_t h, long n) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (n < 0) return fail(h, FVLB_EINVAL, "fvlb_step: n must be >= 0");
   int r = ensure_state(h, true);
+  if (r != FVLB_OK) return r;
+  r = ensure_taup(h);
   if (r != FVLB_OK) return r;
   for (long k = 0; k < n; ++k) {
     StepDesc d = make_desc(h);
@@ -460,6 +495,8 @@ int fvlb_fields(fvlb_t h, int which, double* host_out, size_t count) {
   if (count < need) return fail(h, FVLB_EINVAL, "fvlb_fields: buffer too small");
   int r = ensure_state(h, true);
   if (r != FVLB_OK) return r;
+  r = ensure_taup(h);
+  if (r != FVLB_OK) return r;
   if (!h->fbuf) {
     h->fbuf = static_cast<double*>(dev_alloc(h, sizeof(double) * (size_t)h->N * std::max(h->D, h->C)));
     if (!h->fbuf) return fail(h, FVLB_ENOMEM, "fvlb_fields: device allocation failed");
@@ -478,6 +515,8 @@ int fvlb_reduce(fvlb_t h, double out[8]) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (!out) return fail(h, FVLB_EINVAL, "fvlb_reduce: out is NULL");
   int r = ensure_state(h, true);
+  if (r != FVLB_OK) return r;
+  r = ensure_taup(h);
   if (r != FVLB_OK) return r;
   StepDesc d = make_desc(h);
   cudaError_t e = h->lattice == FVLB_D2Q9 ? fvlb::reduce_d2q9(d, h->part, h->red)
@@ -499,6 +538,8 @@ int fvlb_set_closure(fvlb_t h, fvlb_mlp_t m, double tol) {
   if (m && !(tol >= 0.0)) return fail(h, FVLB_EINVAL, "fvlb_set_closure: tol must be >= 0");
   if (m && h->variant != FVLB_KERNEL_FUSED)
     return fail(h, FVLB_EINVAL, "fvlb_set_closure: the learned closure needs the fused kernel");
+  if (m && h->scheme != FVLB_SCHEME_PRESENT)
+    return fail(h, FVLB_EINVAL, "fvlb_set_closure: the learned closure replaces the present scheme's source");
   int r = ensure_state(h, true);
   if (r != FVLB_OK) return r;
   h->mlp = m;

@@ -34,6 +34,8 @@ struct StepDesc {
   const void* mlp;      // learned closure: packed weights, or null (analytic chi)
   double cl_tol;        // fallback tolerance of the learned closure
   unsigned long long* cl_count;  // [0] nodes on the network, [1] fallbacks
+  int scheme;           // 0 present (f^B), 1 original (stress divergence as a force)
+  void* taup;           // original scheme: C * pitch working-precision values
 };
 
 struct InitDesc {

@@ -149,8 +149,11 @@ __device__ __forceinline__ R pressure(const Phys<R>& ph, const R (&f)[L::Q],
 // HOLD_H keeps all C*Q stress populations in registers (2D); otherwise the
 // conformation is summed in a first pass and each component re-read for its
 // collision (3D, where C*Q = 114).
+// ORIG: the original scheme the paper compares with (Sec. 1, Tables 1-2):
+// no fluctuation term f^B; the caller's F already holds the stress
+// divergence, so it enters u, the pressure and the Guo term as a body force.
 // ---------------------------------------------------------------------------
-template <class L, class S, bool HOLD_H>
+template <class L, class S, bool HOLD_H, bool ORIG = false>
 __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& ph,
                                              const Bufs<S>& b, long long s, int x,
                                              int y, int z, const RT<S> (&u)[L::D],
@@ -191,7 +194,7 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
     uu += u[a] * u[a];
     Fu += F[a] * u[a];
   }
-  const R fB0 = fB_dir<L, R>(0, Ad, kB);
+  const R fB0 = ORIG ? R(0) : fB_dir<L, R>(0, Ad, kB);
   const R p = pressure<L, R>(ph, f, u, F, fB0);
 
   // --- stress source (Sec. 2.3) ---------------------------------------------
@@ -233,7 +236,7 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
     const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
     const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
     const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
-    const R fBi = fB_dir<L, R>(i, Ad, kB);
+    const R fBi = ORIG ? R(0) : fB_dir<L, R>(i, Ad, kB);
     const R fpost = f[i] - (f[i] - feq) * ph.inv_tau_f + fBi + Fi;
     Store<S>::st(b.f_out + j * P + d, fpost, Store<S>::sr ? lcg_next(rng) : 0u);
 
@@ -1158,12 +1161,69 @@ __global__ void __launch_bounds__(FusedShape<L, GX, 1, false>::NT, MINB)
 static __global__ void k_advance_step(long long* t) { *t += 1; }
 
 // ---------------------------------------------------------------------------
-// Split step: velocity field to a device buffer, then collide-and-push with
-// the gradient read from that buffer.  One thread per site.
+// Original scheme (Sec. 1, Tables 1-2): the polymer stress of every node in
+// a working array tau_p[C][pitch], then its divergence by finite
+// differences: central (periodic wrap), and next to a wall the one-sided
+// second-order difference (-3 t0 + 4 t1 - t2) / 2 through the two nodes
+// inside (sign mirrored at the upper wall), since no stress is known at the
+// wall.  Needs 3 nodes across a walled axis.
 // ---------------------------------------------------------------------------
 template <class L, class S>
+__global__ void k_taup(Grid g, Phys<RT<S>> ph, const S* __restrict__ h,
+                       RT<S>* __restrict__ taup, long long N) {
+  using R = RT<S>;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < L::C; ++k) {
+      R a = R(0);  // (A - I)_k from the deviations h'
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) a += load_h<L, S>(h, g.pitch, s, k, i);
+      taup[k * g.pitch + s] = ph.eta_over_lam * a;
+    }
+  }
+}
+
+// dv_b = sum_a d_a tau_ab at node (x, y, z) = s
+template <class L, class R>
+__device__ __forceinline__ void div_taup(const Grid& g, const R* __restrict__ tp, int x, int y,
+                                         int z, long long s, R (&dv)[3]) {
+  const int p[3] = {x, y, z};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
+  dv[0] = dv[1] = dv[2] = R(0);
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    if (n[a] == 1) continue;
+    const bool wall = (g.walls >> a) & 1;
+    const bool edge = wall && (p[a] == 0 || p[a] == n[a] - 1);
+    const long long e = p[a] == 0 ? st[a] : -st[a];
+    const long long sp = p[a] + 1 < n[a] ? s + st[a] : s - (long long)(n[a] - 1) * st[a];
+    const long long sm = p[a] > 0 ? s - st[a] : s + (long long)(n[a] - 1) * st[a];
+#pragma unroll
+    for (int b = 0; b < L::D; ++b) {
+      const R* t = tp + (long long)sym<L>(a, b) * g.pitch;
+      R d;
+      if (edge) {
+        d = R(0.5) * (R(-3) * t[s] + R(4) * t[s + e] - t[s + 2 * e]);
+        if (p[a] != 0) d = -d;
+      } else {
+        d = R(0.5) * (t[sp] - t[sm]);
+      }
+      dv[b] += d;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split step: velocity field to a device buffer, then collide-and-push with
+// the gradient read from that buffer.  One thread per site.  ORIG: the
+// original scheme, the stress divergence added to the body force.
+// ---------------------------------------------------------------------------
+template <class L, class S, bool ORIG = false>
 __global__ void k_velocity(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
-                           RT<S>* __restrict__ ubuf, long long N) {
+                           RT<S>* __restrict__ ubuf, const RT<S>* __restrict__ taup,
+                           long long N) {
   using R = RT<S>;
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
        s += (long long)gridDim.x * blockDim.x) {
@@ -1173,6 +1233,13 @@ __global__ void k_velocity(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
     load_f<L, S>(f, g.pitch, s, fv);
     R F[3];
     body_force<L, R>(ph, x, y, F);
+    if constexpr (ORIG) {
+      R dv[3];
+      div_taup<L, R>(g, taup, x, y, (int)(s / ((long long)g.nx * g.ny)), s, dv);
+      F[0] += dv[0];
+      F[1] += dv[1];
+      F[2] += dv[2];
+    }
     R u[L::D];
     velocity<L, R>(fv, F, u);
 #pragma unroll
@@ -1180,9 +1247,10 @@ __global__ void k_velocity(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
   }
 }
 
-template <class L, class S, bool HOLD_H>
+template <class L, class S, bool HOLD_H, bool ORIG = false>
 __global__ void k_collide_split(Grid g, Phys<RT<S>> ph, Bufs<S> b,
-                                const RT<S>* __restrict__ ubuf, long long N) {
+                                const RT<S>* __restrict__ ubuf, const RT<S>* __restrict__ taup,
+                                long long N) {
   using R = RT<S>;
   constexpr int D = L::D;
   const long long P = g.pitch;
@@ -1215,7 +1283,14 @@ __global__ void k_collide_split(Grid g, Phys<RT<S>> ph, Bufs<S> b,
     load_f<L, S>(b.f_in, P, s, fv);
     R F[3];
     body_force<L, R>(ph, x, y, F);
-    collide_site<L, S, HOLD_H>(g, ph, b, s, x, y, z, u, gr, fv, F);
+    if constexpr (ORIG) {
+      R dv[3];
+      div_taup<L, R>(g, taup, x, y, z, s, dv);
+      F[0] += dv[0];
+      F[1] += dv[1];
+      F[2] += dv[2];
+    }
+    collide_site<L, S, HOLD_H, ORIG>(g, ph, b, s, x, y, z, u, gr, fv, F);
   }
 }
 
@@ -1268,10 +1343,10 @@ __global__ void k_init(Grid g, S* __restrict__ f, S* __restrict__ h,
 // Macroscopic fields of the current state into a device FP64 buffer.
 // which: 0 u [N][D], 1 p [N], 2 A [N][C], 3 tau_p [N][C].
 // ---------------------------------------------------------------------------
-template <class L, class S>
+template <class L, class S, bool ORIG = false>
 __global__ void k_fields(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
                          const S* __restrict__ h, int which, double* __restrict__ out,
-                         long long N) {
+                         const RT<S>* __restrict__ taup, long long N) {
   using R = RT<S>;
   constexpr int D = L::D, Q = L::Q, C = L::C;
   const long long P = g.pitch;
@@ -1283,6 +1358,13 @@ __global__ void k_fields(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
     load_f<L, S>(f, P, s, fv);
     R F[3];
     body_force<L, R>(ph, x, y, F);
+    if constexpr (ORIG) {  // the original scheme: stress divergence in the force
+      R dv[3];
+      div_taup<L, R>(g, taup, x, y, (int)(s / ((long long)g.nx * g.ny)), s, dv);
+      F[0] += dv[0];
+      F[1] += dv[1];
+      F[2] += dv[2];
+    }
     R u[D];
     velocity<L, R>(fv, F, u);
     if (which == 0) {
@@ -1300,7 +1382,7 @@ __global__ void k_fields(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
       tp[k] = ph.eta_over_lam * a;
     }
     if (which == 1) {
-      const R fB0 = fB_dir<L, R>(0, tp, ph.inv_tau_f);
+      const R fB0 = ORIG ? R(0) : fB_dir<L, R>(0, tp, ph.inv_tau_f);
       out[s] = double(pressure<L, R>(ph, fv, u, F, fB0));
     } else if (which == 2) {
 #pragma unroll
@@ -1332,10 +1414,11 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-template <class L, class S>
+template <class L, class S, bool ORIG = false>
 __global__ void __launch_bounds__(kReduceThreads)
     k_reduce_partial(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
-                     const S* __restrict__ h, double* __restrict__ part, long long N) {
+                     const S* __restrict__ h, double* __restrict__ part, long long N,
+                     const RT<S>* __restrict__ taup = nullptr) {
   using R = RT<S>;
   constexpr int D = L::D, Q = L::Q, C = L::C;
   const long long P = g.pitch;
@@ -1358,6 +1441,13 @@ __global__ void __launch_bounds__(kReduceThreads)
     }
     R F[3];
     body_force<L, R>(ph, x, y, F);
+    if constexpr (ORIG) {  // the original scheme: stress divergence in the force
+      R dv[3];
+      div_taup<L, R>(g, taup, x, y, (int)(s / ((long long)g.nx * g.ny)), s, dv);
+      F[0] += dv[0];
+      F[1] += dv[1];
+      F[2] += dv[2];
+    }
     R u[D];
     velocity<L, R>(fv, F, u);
     double uu = 0.0;

@@ -132,6 +132,18 @@ cudaError_t step_impl(const StepDesc& d) {
   Bufs<S> b{static_cast<const S*>(d.f_in), static_cast<S*>(d.f_out),
             static_cast<const S*>(d.h_in), static_cast<S*>(d.h_out),
             static_cast<X*>(d.chi)};
+  if (d.scheme == 1) {
+    // the original scheme: stress array, velocity with the stress divergence
+    // as a body force, collision without f^B (one thread per node each)
+    const int threads = 128;
+    const int blocks = grid_stride_blocks(d.N, threads, d.sms);
+    R* ubuf = static_cast<R*>(d.ubuf);
+    R* taup = static_cast<R*>(d.taup);
+    k_taup<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, b.h_in, taup, d.N);
+    k_velocity<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, taup, d.N);
+    k_collide_split<L, S, true, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, taup, d.N);
+    return cudaGetLastError();
+  }
   if (d.variant == 0) {
     // Shapes measured fastest on GB300 (256^3 D3Q19, 2048^2 D2Q9): 2D four
     // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D FP32
@@ -157,8 +169,8 @@ cudaError_t step_impl(const StepDesc& d) {
     const int threads = 128;
     const int blocks = grid_stride_blocks(d.N, threads, d.sms);
     R* ubuf = static_cast<R*>(d.ubuf);
-    k_velocity<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, d.N);
-    k_collide_split<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, d.N);
+    k_velocity<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, nullptr, d.N);
+    k_collide_split<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, nullptr, d.N);
   }
   return cudaGetLastError();
 }
@@ -181,9 +193,15 @@ cudaError_t fields_impl(const StepDesc& d, int which, double* out) {
   Phys<R> ph = make_phys<R>(d);
   const int threads = 256;
   const int blocks = grid_stride_blocks(d.N, threads, d.sms);
-  k_fields<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, static_cast<const S*>(d.f_in),
-                                                   static_cast<const S*>(d.h_in), which, out,
-                                                   d.N);
+  const S* f = static_cast<const S*>(d.f_in);
+  const S* h = static_cast<const S*>(d.h_in);
+  if (d.scheme == 1) {
+    R* taup = static_cast<R*>(d.taup);
+    k_taup<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, h, taup, d.N);
+    k_fields<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, f, h, which, out, taup, d.N);
+  } else {
+    k_fields<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, f, h, which, out, nullptr, d.N);
+  }
   return cudaGetLastError();
 }
 
@@ -193,8 +211,16 @@ cudaError_t reduce_impl(const StepDesc& d, double* part, double* out) {
   Grid g{d.nx, d.ny, L::D == 3 ? d.nz : 1, d.walls, d.pitch};
   Phys<R> ph = make_phys<R>(d);
   const int nparts = reduce_parts(d.N);
-  k_reduce_partial<L, S><<<nparts, kReduceThreads, 0, d.stream>>>(
-      g, ph, static_cast<const S*>(d.f_in), static_cast<const S*>(d.h_in), part, d.N);
+  const S* f = static_cast<const S*>(d.f_in);
+  const S* h = static_cast<const S*>(d.h_in);
+  if (d.scheme == 1) {
+    R* taup = static_cast<R*>(d.taup);
+    k_taup<L, S><<<grid_stride_blocks(d.N, 256, d.sms), 256, 0, d.stream>>>(g, ph, h, taup, d.N);
+    k_reduce_partial<L, S, true><<<nparts, kReduceThreads, 0, d.stream>>>(g, ph, f, h, part, d.N,
+                                                                          taup);
+  } else {
+    k_reduce_partial<L, S><<<nparts, kReduceThreads, 0, d.stream>>>(g, ph, f, h, part, d.N);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return reduce_finalize(part, nparts, d.N, out, d.stream);

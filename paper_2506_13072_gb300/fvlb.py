@@ -44,6 +44,9 @@ FVLB_BF16_DEV_SR = 5
 FVLB_KERNEL_FUSED = 0
 FVLB_KERNEL_SPLIT = 1
 
+FVLB_SCHEME_PRESENT = 0
+FVLB_SCHEME_ORIGINAL = 1
+
 FVLB_FIELD_U = 0
 FVLB_FIELD_P = 1
 FVLB_FIELD_A = 2
@@ -91,6 +94,7 @@ _SIGS = {
     "fvlb_set_walls": ([_H, ctypes.c_uint], ctypes.c_int),
     "fvlb_set_precision": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_kernel": ([_H, ctypes.c_int], ctypes.c_int),
+    "fvlb_set_scheme": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
     "fvlb_init_fields": ([_H, _dp, _dp, _dp], ctypes.c_int),
     "fvlb_step": ([_H, ctypes.c_long], ctypes.c_int),
@@ -214,7 +218,8 @@ class Simulation:
 
     def __init__(self, lattice, nx, ny, nz=1, tau_s=0.8, eta_p=0.0, lam=1.0,
                  force_kind=FVLB_FORCE_NONE, F0=(0.0, 0.0, 0.0), k=0.0, omega=0.0,
-                 walls=0, precision=FVLB_FP64, kernel=FVLB_KERNEL_FUSED, stream=None):
+                 walls=0, precision=FVLB_FP64, kernel=FVLB_KERNEL_FUSED, stream=None,
+                 scheme=FVLB_SCHEME_PRESENT):
         self.lattice = lattice
         self.D = 2 if lattice == FVLB_D2Q9 else 3
         self.C = 3 if self.D == 2 else 6
@@ -230,6 +235,7 @@ class Simulation:
                               float(tau_s), float(eta_p), float(lam), ctypes.byref(frc)))
         self.h = h
         try:
+            check(lib.fvlb_set_scheme(h, int(scheme)), h)
             check(lib.fvlb_set_walls(h, int(walls)), h)
             if isinstance(precision, str):
                 precision = PRECISIONS[precision]
@@ -274,6 +280,9 @@ class Simulation:
 
     def set_kernel(self, variant):
         check(lib.fvlb_set_kernel(self.h, int(variant)), self.h)
+
+    def set_scheme(self, scheme):
+        check(lib.fvlb_set_scheme(self.h, int(scheme)), self.h)
 
     @property
     def shape(self):

@@ -33,24 +33,26 @@ def compact(A):
     return fvlb().full_to_compact(A)
 
 
-def gpu_sim(pr, precision, kernel=0):
+def gpu_sim(pr, precision, kernel=0, scheme=0):
     F = fvlb()
-    s = F.Simulation.from_problem(pr, precision=precision, kernel=kernel)
+    s = F.Simulation.from_problem(pr, precision=precision, kernel=kernel, scheme=scheme)
     s.init_fields(pr.u0, pr.p0, pr.A0)
     return s
 
 
-def oracle_sim(pr):
-    o = O.Oracle(pr.lattice, **pr.oracle_kwargs())
+def oracle_sim(pr, scheme=0):
+    o = O.Oracle(pr.lattice, scheme=scheme, **pr.oracle_kwargs())
     o.init(u=pr.u0, p=pr.p0, A=pr.A0)
     return o
 
 
-def compare(pr, steps, precision, tol, kernel=0, chunks=1, fields=("u", "p", "tau_p", "A")):
+def compare(pr, steps, precision, tol, kernel=0, chunks=1, fields=("u", "p", "tau_p", "A"),
+            scheme=0):
     """Advance both sides `steps` steps (in `chunks` pieces) and return the
-    worst relative L2 error per field; assert each is <= tol."""
-    s = gpu_sim(pr, precision, kernel)
-    o = oracle_sim(pr)
+    worst relative L2 error per field; assert each is <= tol.  scheme 1: the
+    original scheme on both sides."""
+    s = gpu_sim(pr, precision, kernel, scheme)
+    o = oracle_sim(pr, scheme)
     worst = {k: 0.0 for k in fields}
     per = steps // chunks
     for c in range(chunks):

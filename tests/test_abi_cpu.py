@@ -48,6 +48,7 @@ def test_create_rejects_unknown_force():
 def test_null_handle_calls_fail_cleanly():
     assert F.lib.fvlb_step(None, 1) == F.FVLB_EINVAL
     assert F.lib.fvlb_set_walls(None, 1) == F.FVLB_EINVAL
+    assert F.lib.fvlb_set_scheme(None, 1) == F.FVLB_EINVAL
     assert F.lib.fvlb_destroy(None) == F.FVLB_OK
     assert isinstance(F.lib.fvlb_last_error(None), bytes)
 
