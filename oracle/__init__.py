@@ -35,6 +35,13 @@ FIELD_TAU_P = 3
 SCHEME_PRESENT = 0
 SCHEME_ORIGINAL = 1
 
+# constitutive model (reading R9 of fvlb_oracle.c); its parameter is alpha
+# (Giesekus) or eps (PTT)
+MODEL_OLDROYD_B = 0
+MODEL_GIESEKUS = 1
+MODEL_PTT_LINEAR = 2
+MODEL_PTT_EXP = 3
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fvlb_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
@@ -76,6 +83,8 @@ def lib():
             L.orc_set_tau_h.argtypes = [ctypes.c_void_p, ctypes.c_double]
             L.orc_set_scheme.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_set_scheme.restype = ctypes.c_int
+            L.orc_set_model.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
+            L.orc_set_model.restype = ctypes.c_int
             L.orc_time.argtypes = [ctypes.c_void_p]
             L.orc_time.restype = ctypes.c_long
             L.orc_init.argtypes = [ctypes.c_void_p, dp, dp, dp]
@@ -191,7 +200,8 @@ class Oracle:
 
     def __init__(self, lat, nx, ny, nz=1, tau_s=0.8, eta_p=0.0, lam=1.0,
                  force_kind=FORCE_NONE, F0=(0.0, 0.0, 0.0), k=0.0, omega=0.0,
-                 walls=0, tau_h=None, scheme=SCHEME_PRESENT):
+                 walls=0, tau_h=None, scheme=SCHEME_PRESENT, model=MODEL_OLDROYD_B,
+                 mpar=0.0):
         self.lat = lat
         self.D = 2 if lat == D2Q9 else 3
         self.Q = qsize(lat)
@@ -209,6 +219,10 @@ class Oracle:
             lib().orc_destroy(self._h)
             self._h = None
             raise ValueError("invalid scheme")
+        if lib().orc_set_model(self._h, int(model), float(mpar)) != 0:
+            lib().orc_destroy(self._h)
+            self._h = None
+            raise ValueError("invalid constitutive model")
         if lib().orc_set_walls(self._h, int(walls)) != 0:
             lib().orc_destroy(self._h)
             self._h = None

@@ -42,6 +42,17 @@
  *       (-3 t0 + 4 t1 - t2) / 2 (sign mirrored at the upper wall), since no
  *       stress is known at the wall.  The total force enters u, the Guo
  *       term and the pressure as the body force does in the present scheme.
+ *   R9  Other constitutive models (the paper names Giesekus and
+ *       Phan-Thien-Tanner in Sec. 1 and leaves them to future work in
+ *       Sec. 4) change only the relaxation part of chi (Sec. 2.3):
+ *       chi = -P(A)/lambda + A.grad u + (grad u)^T.A, with M = A - I and
+ *         Oldroyd-B          P = M
+ *         Giesekus (alpha)   P = M + alpha M.M
+ *         linear PTT (eps)   P = (1 + eps tr M) M
+ *         exponential PTT    P = exp(eps tr M) M
+ *       (PTT without the slip parameter), tau_p = (eta_p/lambda) M in all
+ *       four.  The trace runs over the D x D tensor; in 2D A_zz = 1, so M has
+ *       no z entries and the 2D restriction is exact.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -254,6 +265,9 @@ typedef struct orc {
   double *u;         /* [N][3] velocity of the current step */
   double *A;         /* [N][DD] conformation of the current step */
   int scheme;        /* 0: present (f^B), 1: original (div tau_p as a force) */
+  int model;         /* constitutive model (reading R9): 0 Oldroyd-B,
+                        1 Giesekus, 2 linear PTT, 3 exponential PTT */
+  double mpar;       /* its parameter: alpha (Giesekus) or eps (PTT) */
   double *divt;      /* [N][3] div tau_p of the current step (scheme 1) */
   int first;
   long t;
@@ -353,6 +367,14 @@ int orc_set_scheme(orc *o, int scheme) {
     for (int a = 0; a < 3; ++a)
       if (o->walls[a] && o->n[a] < 3) return -1;
   o->scheme = scheme;
+  return 0;
+}
+
+/* Constitutive model (reading R9) and its parameter. */
+int orc_set_model(orc *o, int model, double par) {
+  if (model < 0 || model > 3 || !(par >= 0.0)) return -1;
+  o->model = model;
+  o->mpar = par;
   return 0;
 }
 
@@ -457,6 +479,34 @@ static void moments_sweep(orc *o) {
       }
 }
 
+/* Relaxation part P(A) of chi (Sec. 2.3; other models: reading R9), full
+ * D x D tensor. */
+static void relax_term(const orc *o, const double *A, double *P) {
+  const int D = o->D;
+  double M[9];
+  double tr = 0.0;
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) M[T(D, a, b)] = A[T(D, a, b)] - (a == b ? 1.0 : 0.0);
+  for (int a = 0; a < D; ++a) tr += M[T(D, a, a)];
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) {
+      const double m = M[T(D, a, b)];
+      double v;
+      if (o->model == 1) {
+        double mm = 0.0;
+        for (int g = 0; g < D; ++g) mm += M[T(D, a, g)] * M[T(D, g, b)];
+        v = m + o->mpar * mm;
+      } else if (o->model == 2) {
+        v = (1.0 + o->mpar * tr) * m;
+      } else if (o->model == 3) {
+        v = exp(o->mpar * tr) * m;
+      } else {
+        v = m;
+      }
+      P[T(D, a, b)] = v;
+    }
+}
+
 /* d u_b / d x_a at node p (reading R2). */
 static double grad_component(const orc *o, const int p[3], int a, int b) {
   const int n = o->n[a];
@@ -512,7 +562,7 @@ static long stream_dest(const orc *o, const int p[3], int i, int *i_out) {
 static void step_once(orc *o) {
   const lattice_t *L = &o->L;
   const int Q = o->Q, D = o->D, DD = o->DD;
-  double fB[19], Fi[19], feq[19], tau_p[9], grad[9], chi[9];
+  double fB[19], Fi[19], feq[19], tau_p[9], grad[9], chi[9], relax[9];
 
   moments_sweep(o);
 
@@ -540,12 +590,14 @@ static void step_once(orc *o) {
         const double pr = pressure_site(L, o->tau_f, f, u, Fi[0], fB[0]);
         feq_site(L, pr, u, feq);
 
-        /* grad u and chi = -(A - I)/lambda + A.grad u + (grad u)^T.A */
+        /* grad u and chi = -P(A)/lambda + A.grad u + (grad u)^T.A, with
+         * P(A) = A - I for Oldroyd-B (Sec. 2.3) or the model of reading R9 */
         for (int a = 0; a < D; ++a)
           for (int b = 0; b < D; ++b) grad[T(D, a, b)] = grad_component(o, p, a, b);
+        relax_term(o, A, relax);
         for (int a = 0; a < D; ++a)
           for (int b = 0; b < D; ++b) {
-            double v = -(A[T(D, a, b)] - (a == b ? 1.0 : 0.0)) / o->lambda;
+            double v = -relax[T(D, a, b)] / o->lambda;
             for (int g = 0; g < D; ++g) {
               v += A[T(D, a, g)] * grad[T(D, g, b)];
               v += grad[T(D, g, a)] * A[T(D, g, b)];

@@ -58,6 +58,10 @@ class Problem:
     p0: np.ndarray | None = None
     A0: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
+    # constitutive model: 0 Oldroyd-B (the paper's), 1 Giesekus, 2 linear
+    # PTT, 3 exponential PTT; mpar is alpha (Giesekus) or eps (PTT)
+    model: int = 0
+    mpar: float = 0.0
 
     @property
     def D(self) -> int:
@@ -74,7 +78,8 @@ class Problem:
     def oracle_kwargs(self) -> dict:
         return dict(nx=self.nx, ny=self.ny, nz=self.nz, tau_s=self.tau_s,
                     eta_p=self.eta_p, lam=self.lam, force_kind=self.force_kind,
-                    F0=self.F0, k=self.k, omega=self.omega, walls=self.walls)
+                    F0=self.F0, k=self.k, omega=self.omega, walls=self.walls,
+                    model=self.model, mpar=self.mpar)
 
 
 def _coords(shape):

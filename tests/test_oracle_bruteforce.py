@@ -174,7 +174,13 @@ class NumpyLB:
                                 + pr.tau_s * fB[..., 0])
         fpost = f - (f - self.feq(p, u)) / pr.tau_s + fB + Fi
         g = self.grad(u)
-        chi = -(A - I) / pr.lam + np.einsum("...ag,...gb->...ab", A, g) \
+        M = A - I
+        trM = np.trace(M, axis1=-2, axis2=-1)[..., None, None]
+        relax = {0: lambda: M,
+                 1: lambda: M + pr.mpar * np.einsum("...ag,...gb->...ab", M, M),
+                 2: lambda: (1 + pr.mpar * trM) * M,
+                 3: lambda: np.exp(pr.mpar * trM) * M}[pr.model]()
+        chi = -relax / pr.lam + np.einsum("...ag,...gb->...ab", A, g) \
             + np.einsum("...ga,...gb->...ab", g, A)
         if self.first:
             self.chi_old = chi.copy()
@@ -245,3 +251,20 @@ def test_bruteforce_d3q19(walls):
                    (1e-5, 2e-5, -1e-5), walls=walls)
     pr.u0, pr.p0, pr.A0 = W.random_smooth(W.D3Q19, pr.shape, seed=14, U=0.03, dA=0.5)
     _compare(pr, 12)
+
+
+@pytest.mark.parametrize("model,par", [(O.MODEL_GIESEKUS, 0.3), (O.MODEL_PTT_LINEAR, 0.4),
+                                       (O.MODEL_PTT_EXP, 0.4)])
+@pytest.mark.parametrize("lat", [W.D2Q9, W.D3Q19])
+def test_bruteforce_models(lat, model, par):
+    """Other constitutive models (reading R9 of the oracle): the relaxation
+    part of chi, by full-tensor einsum, in a walled random flow."""
+    if lat == W.D2Q9:
+        pr = W.Problem("bf", W.D2Q9, 7, 6, 1, 0.8, 0.2, 6.0, W.FORCE_CONST, (2e-5, -1e-5, 0.0),
+                       walls=0b10)
+    else:
+        pr = W.Problem("bf3", W.D3Q19, 5, 4, 6, 0.75, 0.15, 6.0, W.FORCE_CONST,
+                       (1e-5, 2e-5, -1e-5), walls=0b001)
+    pr.model, pr.mpar = model, par
+    pr.u0, pr.p0, pr.A0 = W.random_smooth(lat, pr.shape, seed=21, U=0.03, dA=0.6)
+    _compare(pr, 15)
