@@ -437,6 +437,13 @@ def run_ours(args, rank, world, dist):
         for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("fp32", F.FVLB_FP32)):
             forms[f"batched_512_d2q9_{name}"] = batch_rate(F, prec, stream)
             torch.cuda.empty_cache()
+        # other constitutive models (relaxation part of chi): same bytes per update
+        for name, model, par in (("giesekus", F.FVLB_MODEL_GIESEKUS, 0.3),
+                                 ("ptt_exp", F.FVLB_MODEL_PTT_EXP, 0.25)):
+            pm = tgv_problem(WORKLOAD["n"])
+            pm.model, pm.mpar = model, par
+            forms[f"d3q19_256^3_fp32_{name}"] = form_rate(F, pm, F.FVLB_FP32, K, 2, stream)
+            torch.cuda.empty_cache()
         forms["d3q19_256^3_fp32_learned_closure"] = closure_rate(F, stream)
         torch.cuda.empty_cache()
         for k, v in forms.items():

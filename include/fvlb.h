@@ -103,6 +103,17 @@ enum { FVLB_KERNEL_FUSED = 0, FVLB_KERNEL_SPLIT = 1 };
  * stress divergence added to the body force. */
 enum { FVLB_SCHEME_PRESENT = 0, FVLB_SCHEME_ORIGINAL = 1 };
 
+/* Constitutive model of the polymer (fvlb_set_model).  The paper solves
+ * Oldroyd-B (Sec. 2.1) and names Giesekus and Phan-Thien-Tanner as the other
+ * common differential models (Sec. 1, future work in Sec. 4); they differ
+ * only in the relaxation part of the stress source chi of Sec. 2.3. */
+enum {
+  FVLB_MODEL_OLDROYD_B = 0,
+  FVLB_MODEL_GIESEKUS = 1,
+  FVLB_MODEL_PTT_LINEAR = 2,
+  FVLB_MODEL_PTT_EXP = 3
+};
+
 /* Fields for fvlb_fields. */
 enum {
   FVLB_FIELD_U = 0,    /* u = sum_{i!=0} c_i f_i + F/2 (Sec. 2.2)            */
@@ -167,6 +178,21 @@ int fvlb_set_kernel(fvlb_t h, int variant);
  * total force.  FVLB_EINVAL for an unknown scheme, for a walled axis of
  * fewer than 3 nodes, or while a learned closure is attached. */
 int fvlb_set_scheme(fvlb_t h, int scheme);
+
+/* Constitutive model and its parameter; may be changed between steps.  With
+ * M = A - I the stress source is chi = -P(M)/lambda + A.grad u +
+ * (grad u)^T.A (Sec. 2.3) and P is
+ *   FVLB_MODEL_OLDROYD_B   M                      (param ignored; default)
+ *   FVLB_MODEL_GIESEKUS    M + alpha M.M           (param = alpha in [0, 1])
+ *   FVLB_MODEL_PTT_LINEAR  (1 + eps tr M) M        (param = eps >= 0)
+ *   FVLB_MODEL_PTT_EXP     exp(eps tr M) M         (param = eps >= 0)
+ * (PTT without the slip parameter); tau_p = (eta_p/lambda) M in every model,
+ * so f^B, the original scheme's body force, the fields and the diagnostics
+ * are unchanged.  Every kernel variant, storage and scheme takes it.
+ * FVLB_EINVAL for an unknown model, a negative or non-finite parameter, a
+ * Giesekus alpha above 1, or a non-Oldroyd-B model while a learned closure
+ * is attached (the network stands for the Oldroyd-B source). */
+int fvlb_set_model(fvlb_t h, int model, double param);
 
 /* CUDA stream (a cudaStream_t, or NULL for the legacy default stream) on
  * which all later GPU work of the handle is enqueued. */

@@ -71,6 +71,8 @@ struct fvlb_s {
   unsigned long long* cl_count = nullptr;  // [0] network nodes, [1] fallbacks
   int scheme = FVLB_SCHEME_PRESENT;
   void* taup = nullptr;     // original scheme: polymer stress working array
+  int model = FVLB_MODEL_OLDROYD_B;
+  double mpar = 0.0;        // alpha (Giesekus) or eps (PTT)
   fvlb_alloc_fn alloc = nullptr;
   fvlb_free_fn free_ = nullptr;
   void* actx = nullptr;
@@ -155,6 +157,8 @@ StepDesc make_desc(fvlb_t h) {
   d.cl_count = h->cl_count;
   d.scheme = h->scheme;
   d.taup = h->taup;
+  d.model = h->model;
+  d.mpar = h->mpar;
   double c = 0.0;
   if (h->force.kind == FVLB_FORCE_CONST) c = 1.0;
   if (h->force.kind == FVLB_FORCE_COSINE) c = std::cos(h->force.omega * (double)h->t);
@@ -426,6 +430,21 @@ int fvlb_set_scheme(fvlb_t h, int scheme) {
   return FVLB_OK;
 }
 
+int fvlb_set_model(fvlb_t h, int model, double param) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  if (model < FVLB_MODEL_OLDROYD_B || model > FVLB_MODEL_PTT_EXP)
+    return fail(h, FVLB_EINVAL, "fvlb_set_model: unknown model");
+  if (!(param >= 0.0) || !std::isfinite(param))
+    return fail(h, FVLB_EINVAL, "fvlb_set_model: the parameter must be finite and >= 0");
+  if (model == FVLB_MODEL_GIESEKUS && param > 1.0)
+    return fail(h, FVLB_EINVAL, "fvlb_set_model: the Giesekus mobility must be <= 1");
+  if (model != FVLB_MODEL_OLDROYD_B && h->mlp)
+    return fail(h, FVLB_EINVAL, "fvlb_set_model: a learned closure is attached");
+  h->model = model;
+  h->mpar = model == FVLB_MODEL_OLDROYD_B ? 0.0 : param;
+  return FVLB_OK;
+}
+
 int fvlb_set_precision(fvlb_t h, int storage) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (storage < FVLB_FP64 || storage > FVLB_BF16_DEV_SR)
@@ -540,6 +559,8 @@ int fvlb_set_closure(fvlb_t h, fvlb_mlp_t m, double tol) {
     return fail(h, FVLB_EINVAL, "fvlb_set_closure: the learned closure needs the fused kernel");
   if (m && h->scheme != FVLB_SCHEME_PRESENT)
     return fail(h, FVLB_EINVAL, "fvlb_set_closure: the learned closure replaces the present scheme's source");
+  if (m && h->model != FVLB_MODEL_OLDROYD_B)
+    return fail(h, FVLB_EINVAL, "fvlb_set_closure: the learned closure stands for the Oldroyd-B source");
   int r = ensure_state(h, true);
   if (r != FVLB_OK) return r;
   h->mlp = m;

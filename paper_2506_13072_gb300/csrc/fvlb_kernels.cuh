@@ -203,7 +203,7 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
     R A[C], chi[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) A[k] = Ad[k] + (diag<L>(k) ? R(1) : R(0));
-    chi_tensor<L, R>(A, Ad, gr, ph.inv_lam, chi);
+    chi_tensor<L, R>(A, Ad, gr, ph, chi);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       R old = R(b.chi[k * P + s]);
@@ -854,7 +854,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         bool used = false;
         if (active) {
           R chi_an[C];
-          chi_tensor<L, R>(A, Ad, gr, ph.inv_lam, chi_an);
+          chi_tensor<L, R>(A, Ad, gr, ph, chi_an);
           float num = 0.f, den = 0.f;
           float chi_nn[C];
 #pragma unroll
@@ -923,7 +923,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       // k (warp-uniform), so that every population index and coefficient
       // in it is a compile-time constant.
       // stress source of this component (Sec. 2.3):
-      // chi_ab = -(A - I)_ab / lambda + sum_r (A_ar d_r u_b + d_r u_a A_rb)
+      // chi_ab = -P_ab / lambda + sum_r (A_ar d_r u_b + d_r u_a A_rb), with
+      // P = A - I for Oldroyd-B (relax_part for the other models)
       R chi_k = R(0), Ad_k = R(0), A_k = R(0);
       on_component(k, [&](auto KC) {
         constexpr int q = decltype(KC)::value;
@@ -934,7 +935,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
             chi_k = cls.chi[q][nd];
           } else {
             constexpr int a = L::ca(q), bb = L::cb(q);
-            R v = -Ad[q] * ph.inv_lam;
+            R v = -(ph.model ? relax_part<L, R>(q, Ad, ph.model, ph.mpar) : Ad[q]) * ph.inv_lam;
 #pragma unroll
             for (int r = 0; r < D; ++r) {
               // d_r u_a and d_r u_b from the ring (central, or one-sided at walls)

@@ -271,6 +271,8 @@ struct Phys {
   const void* mlp;    // learned closure: packed network weights (or null)
   float cl_tol2;      // squared fallback tolerance of the learned closure
   unsigned long long* cl_count;  // [0] nodes on the network, [1] fallbacks
+  int model;          // constitutive model: 0 Oldroyd-B, 1 Giesekus, 2 / 3 PTT
+  R mpar;             // its parameter: alpha (Giesekus) or eps (PTT)
 };
 
 template <class S>
@@ -359,14 +361,39 @@ __device__ __forceinline__ R fB_dir(int i, const R (&t)[L::C], R inv_tau_f) {
 
 // (grad u)_{ab} = d_a u_b, chi = -(A - I)/lambda + A.grad u + (grad u)^T.A
 // in compact components (Sec. 2.3); Ad = A - I.
+__device__ __forceinline__ float rexp(float x) { return expf(x); }
+__device__ __forceinline__ double rexp(double x) { return exp(x); }
+
+// Relaxation part P of the stress source chi = -P / lambda + A.grad u +
+// (grad u)^T.A (Sec. 2.3), component k, from M = A - I (Ad): the paper's
+// Oldroyd-B model P = M, or one of the models it names beside it (Sec. 1):
+// Giesekus P = M + alpha M.M, linear PTT P = (1 + eps tr M) M, exponential
+// PTT P = exp(eps tr M) M (no slip parameter).  In 2D M has no z entries.
+template <class L, class R>
+__device__ __forceinline__ R relax_part(int k, const R (&Ad)[L::C], int model, R par) {
+  const R m = Ad[k];
+  if (model == 0) return m;
+  if (model == 1) {
+    const int a = L::ca(k), b = L::cb(k);
+    R mm = R(0);
+#pragma unroll
+    for (int g = 0; g < L::D; ++g) mm += Ad[sym<L>(a, g)] * Ad[sym<L>(g, b)];
+    return m + par * mm;
+  }
+  R tr = R(0);
+#pragma unroll
+  for (int g = 0; g < L::D; ++g) tr += Ad[sym<L>(g, g)];
+  return (model == 2 ? R(1) + par * tr : rexp(par * tr)) * m;
+}
+
 template <class L, class R>
 __device__ __forceinline__ void chi_tensor(const R (&A)[L::C], const R (&Ad)[L::C],
-                                           const R (&g)[L::D][L::D], R inv_lam,
+                                           const R (&g)[L::D][L::D], const Phys<R>& ph,
                                            R (&chi)[L::C]) {
 #pragma unroll
   for (int k = 0; k < L::C; ++k) {
     const int a = L::ca(k), b = L::cb(k);
-    R v = -Ad[k] * inv_lam;
+    R v = -relax_part<L, R>(k, Ad, ph.model, ph.mpar) * ph.inv_lam;
 #pragma unroll
     for (int q = 0; q < L::D; ++q) {
       v += A[sym<L>(a, q)] * g[q][b] + g[q][a] * A[sym<L>(q, b)];

@@ -52,6 +52,8 @@ Phys<R> make_phys(const StepDesc& d) {
   p.mlp = d.mlp;
   p.cl_tol2 = float(d.cl_tol * d.cl_tol);
   p.cl_count = d.cl_count;
+  p.model = d.model;
+  p.mpar = R(d.mpar);
   return p;
 }
 

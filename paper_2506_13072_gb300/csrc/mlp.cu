@@ -78,7 +78,7 @@ __global__ void k_closure_pairs(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
       A[k] = a + (diag<L>(k) ? R(1) : R(0));
     }
     R chi[C];
-    chi_tensor<L, R>(A, Ad, gr, ph.inv_lam, chi);
+    chi_tensor<L, R>(A, Ad, gr, ph, chi);
     float* xr = X + j * IN;
     int q = 0;
 #pragma unroll

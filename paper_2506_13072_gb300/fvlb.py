@@ -46,6 +46,10 @@ FVLB_KERNEL_SPLIT = 1
 
 FVLB_SCHEME_PRESENT = 0
 FVLB_SCHEME_ORIGINAL = 1
+FVLB_MODEL_OLDROYD_B = 0
+FVLB_MODEL_GIESEKUS = 1
+FVLB_MODEL_PTT_LINEAR = 2
+FVLB_MODEL_PTT_EXP = 3
 
 FVLB_FIELD_U = 0
 FVLB_FIELD_P = 1
@@ -95,6 +99,7 @@ _SIGS = {
     "fvlb_set_precision": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_kernel": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_scheme": ([_H, ctypes.c_int], ctypes.c_int),
+    "fvlb_set_model": ([_H, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "fvlb_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
     "fvlb_init_fields": ([_H, _dp, _dp, _dp], ctypes.c_int),
     "fvlb_step": ([_H, ctypes.c_long], ctypes.c_int),
@@ -219,7 +224,7 @@ class Simulation:
     def __init__(self, lattice, nx, ny, nz=1, tau_s=0.8, eta_p=0.0, lam=1.0,
                  force_kind=FVLB_FORCE_NONE, F0=(0.0, 0.0, 0.0), k=0.0, omega=0.0,
                  walls=0, precision=FVLB_FP64, kernel=FVLB_KERNEL_FUSED, stream=None,
-                 scheme=FVLB_SCHEME_PRESENT):
+                 scheme=FVLB_SCHEME_PRESENT, model=FVLB_MODEL_OLDROYD_B, mpar=0.0):
         self.lattice = lattice
         self.D = 2 if lattice == FVLB_D2Q9 else 3
         self.C = 3 if self.D == 2 else 6
@@ -236,6 +241,7 @@ class Simulation:
         self.h = h
         try:
             check(lib.fvlb_set_scheme(h, int(scheme)), h)
+            check(lib.fvlb_set_model(h, int(model), float(mpar)), h)
             check(lib.fvlb_set_walls(h, int(walls)), h)
             if isinstance(precision, str):
                 precision = PRECISIONS[precision]
@@ -250,6 +256,8 @@ class Simulation:
 
     @classmethod
     def from_problem(cls, pr, **kw):
+        kw.setdefault("model", getattr(pr, "model", FVLB_MODEL_OLDROYD_B))
+        kw.setdefault("mpar", getattr(pr, "mpar", 0.0))
         s = cls(pr.lattice, pr.nx, pr.ny, pr.nz, pr.tau_s, pr.eta_p, pr.lam, pr.force_kind,
                 pr.F0, pr.k, pr.omega, pr.walls, **kw)
         return s
@@ -283,6 +291,9 @@ class Simulation:
 
     def set_scheme(self, scheme):
         check(lib.fvlb_set_scheme(self.h, int(scheme)), self.h)
+
+    def set_model(self, model, mpar=0.0):
+        check(lib.fvlb_set_model(self.h, int(model), float(mpar)), self.h)
 
     @property
     def shape(self):
