@@ -227,6 +227,21 @@ int fvlb_fields(fvlb_t h, int which, double *host_out, size_t count);
  * Returns FVLB_EUNSTABLE (with out filled) if out[6] > 0. */
 int fvlb_reduce(fvlb_t h, double out[8]);
 
+/* Conformation check of the current state, FP64, on the GPU, synchronising
+ * the handle's stream.  A must stay symmetric positive definite (Sec. 2.1;
+ * it is the covariance of the polymer end-to-end vector), and losing that
+ * is how runs fail at high Wi (the four-roll mill of Sec. 3.1 reaches
+ * Wi = 5).  Per node the smallest eigenvalue of A (2D: closed form; 3D:
+ * Jacobi plane rotations, six sweeps; both accurate to rounding relative to
+ * |A|):
+ *   out[0]   number of nodes whose smallest eigenvalue is not > 0
+ *            (nodes with a non-finite A included)
+ *   out[1]   smallest eigenvalue over the grid (non-finite nodes skipped)
+ *   out[2]   largest tr A over the grid (Sec. 3.1 plots tr A)
+ * Deterministic.  Uses the handle's reduction scratch; allocates the state
+ * (at rest) if needed. */
+int fvlb_conformation(fvlb_t h, double out[3]);
+
 /* The diagnostics of fvlb_reduce for a state the caller holds in its own
  * device memory, with no device allocation at all.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

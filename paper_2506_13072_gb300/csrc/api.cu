@@ -548,6 +548,21 @@ int fvlb_reduce(fvlb_t h, double out[8]) {
   return FVLB_OK;
 }
 
+int fvlb_conformation(fvlb_t h, double out[3]) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  if (!out) return fail(h, FVLB_EINVAL, "fvlb_conformation: out is NULL");
+  int r = ensure_state(h, true);
+  if (r != FVLB_OK) return r;
+  StepDesc d = make_desc(h);
+  cudaError_t e = h->lattice == FVLB_D2Q9 ? fvlb::conformation_d2q9(d, h->part, h->red)
+                                          : fvlb::conformation_d3q19(d, h->part, h->red);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, h->red, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_conformation");
+  return FVLB_OK;
+}
+
 int fvlb_set_closure(fvlb_t h, fvlb_mlp_t m, double tol) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (m && fvlb::mlp_lattice(m) != h->lattice)

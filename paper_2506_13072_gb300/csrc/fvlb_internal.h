@@ -66,6 +66,9 @@ cudaError_t fields_d3q19(const StepDesc& d, int which, double* out);
 int reduce_parts(long long N);
 cudaError_t reduce_d2q9(const StepDesc& d, double* part, double* out);
 cudaError_t reduce_d3q19(const StepDesc& d, double* part, double* out);
+// conformation check: part as for the diagnostics, out[3] as fvlb_conformation
+cudaError_t conformation_d2q9(const StepDesc& d, double* part, double* out);
+cudaError_t conformation_d3q19(const StepDesc& d, double* part, double* out);
 cudaError_t reduce_finalize(const double* part, int nparts, long long N, double* out,
                             cudaStream_t stream);
 // record the message returned by fvlb_last_error(NULL); returns code

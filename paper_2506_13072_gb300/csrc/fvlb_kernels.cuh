@@ -1526,4 +1526,127 @@ static __global__ void __launch_bounds__(kReduceThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Conformation check.  A = I + M must stay symmetric positive definite in
+// every model; losing it is how a run at high Wi fails (the four-roll mill
+// of Sec. 3.1 goes up to Wi = 5).  Per node the smallest eigenvalue of A:
+// in 2D the closed form of a symmetric 2 x 2 matrix, in 3D the Jacobi
+// eigenvalue method (plane rotations; accurate to rounding relative to |A|
+// also for nearly repeated eigenvalues, where roots of the characteristic
+// cubic lose half the digits).  Per block: number of
+// nodes whose smallest eigenvalue is not > 0 (non-finite included), the
+// smallest eigenvalue, the largest tr A.
+// ---------------------------------------------------------------------------
+template <class L>
+__device__ __forceinline__ double min_eigenvalue(const double (&M)[L::C]) {
+  constexpr int D = L::D;
+  if constexpr (D == 2) {
+    const double a = 1.0 + M[sym<L>(0, 0)], c = 1.0 + M[sym<L>(1, 1)], b = M[sym<L>(0, 1)];
+    const double h = 0.5 * (a - c);
+    return 0.5 * (a + c) - sqrt(h * h + b * b);
+  } else {
+    // cyclic Jacobi rotations: each zeroes one off-diagonal entry; six
+    // sweeps of the three pairs take a 3 x 3 matrix to diagonal in double
+    double a[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a[r][c] = M[sym<L>(r, c)] + (r == c ? 1.0 : 0.0);
+#pragma unroll 1
+    for (int sweep = 0; sweep < 6; ++sweep) {
+#pragma unroll
+      for (int pr = 0; pr < 3; ++pr) {
+        const int p = pr == 2 ? 1 : 0, q = pr == 0 ? 1 : 2, o = 3 - p - q;
+        const double apq = a[p][q];
+        if (apq == 0.0) continue;
+        const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+        const double t = copysign(1.0, th) / (fabs(th) + hypot(th, 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        a[p][p] -= t * apq;
+        a[q][q] += t * apq;
+        a[p][q] = a[q][p] = 0.0;
+        const double aop = a[o][p], aoq = a[o][q];
+        a[o][p] = a[p][o] = c * aop - sn * aoq;
+        a[o][q] = a[q][o] = sn * aop + c * aoq;
+      }
+    }
+    return fmin(a[0][0], fmin(a[1][1], a[2][2]));
+  }
+}
+
+template <class L, class S>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_conf_partial(Grid g, const S* __restrict__ h, double* __restrict__ part, long long N) {
+  constexpr int Q = L::Q, C = L::C;
+  const long long P = g.pitch;
+  double cnt = 0.0, emin = INFINITY, trmax = -INFINITY;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    double M[C];
+    double tr = 0.0;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      double a = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a += double(load_h<L, S>(h, P, s, k, i));
+      M[k] = a;
+      if (L::ca(k) == L::cb(k)) tr += 1.0 + a;
+    }
+    const double e = min_eigenvalue<L>(M);
+    cnt += (e > 0.0) ? 0.0 : 1.0;
+    emin = fmin(emin, e);
+    trmax = fmax(trmax, tr);
+  }
+  __shared__ double sm[kReduceThreads / 32][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double v0 = warp_sum(cnt), v1 = -warp_max(-emin), v2 = warp_max(trmax);
+  if (lane == 0) {
+    sm[wid][0] = v0;
+    sm[wid][1] = v1;
+    sm[wid][2] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = sm[0][0], mn = sm[0][1], mx = sm[0][2];
+    for (int w = 1; w < kReduceThreads / 32; ++w) {
+      c += sm[w][0];
+      mn = fmin(mn, sm[w][1]);
+      mx = fmax(mx, sm[w][2]);
+    }
+    part[blockIdx.x * 3 + 0] = c;
+    part[blockIdx.x * 3 + 1] = mn;
+    part[blockIdx.x * 3 + 2] = mx;
+  }
+}
+
+// (static: each translation unit that launches it has its own copy.)
+static __global__ void __launch_bounds__(kReduceThreads)
+    k_conf_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  double c = 0.0, mn = INFINITY, mx = -INFINITY;
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+    c += part[p * 3 + 0];
+    mn = fmin(mn, part[p * 3 + 1]);
+    mx = fmax(mx, part[p * 3 + 2]);
+  }
+  __shared__ double sm[kReduceThreads / 32][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double v0 = warp_sum(c), v1 = -warp_max(-mn), v2 = warp_max(mx);
+  if (lane == 0) {
+    sm[wid][0] = v0;
+    sm[wid][1] = v1;
+    sm[wid][2] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kReduceThreads / 32; ++w) {
+      sm[0][0] += sm[w][0];
+      sm[0][1] = fmin(sm[0][1], sm[w][1]);
+      sm[0][2] = fmax(sm[0][2], sm[w][2]);
+    }
+    out[0] = sm[0][0];
+    out[1] = sm[0][1];
+    out[2] = sm[0][2];
+  }
+}
+
 }  // namespace fvlb

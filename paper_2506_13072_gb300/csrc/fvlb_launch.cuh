@@ -228,6 +228,18 @@ cudaError_t reduce_impl(const StepDesc& d, double* part, double* out) {
   return reduce_finalize(part, nparts, d.N, out, d.stream);
 }
 
+template <class L, class S>
+cudaError_t conf_impl(const StepDesc& d, double* part, double* out) {
+  Grid g{d.nx, d.ny, L::D == 3 ? d.nz : 1, d.walls, d.pitch};
+  const int nparts = reduce_parts(d.N);
+  k_conf_partial<L, S><<<nparts, kReduceThreads, 0, d.stream>>>(
+      g, static_cast<const S*>(d.h_in), part, d.N);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_conf_final<<<1, kReduceThreads, 0, d.stream>>>(part, nparts, out);
+  return cudaGetLastError();
+}
+
 // step_impl is instantiated per (lattice, storage) in its own translation
 // unit (k_step_<lattice>_<storage>.cu) so that the library builds in parallel.
 #define FVLB_EXTERN_STEP(L)                                                   \

@@ -31,4 +31,10 @@ cudaError_t reduce_d2q9(const StepDesc& d, double* part, double* out) {
 #undef CALL
 }
 
+cudaError_t conformation_d2q9(const StepDesc& d, double* part, double* out) {
+#define CALL(S) conf_impl<D2Q9, S>(d, part, out)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
 }  // namespace fvlb

@@ -31,4 +31,10 @@ cudaError_t reduce_d3q19(const StepDesc& d, double* part, double* out) {
 #undef CALL
 }
 
+cudaError_t conformation_d3q19(const StepDesc& d, double* part, double* out) {
+#define CALL(S) conf_impl<D3Q19, S>(d, part, out)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
 }  // namespace fvlb

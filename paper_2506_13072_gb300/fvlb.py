@@ -100,6 +100,7 @@ _SIGS = {
     "fvlb_set_kernel": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_scheme": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_model": ([_H, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+    "fvlb_conformation": ([_H, _dp], ctypes.c_int),
     "fvlb_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
     "fvlb_init_fields": ([_H, _dp, _dp, _dp], ctypes.c_int),
     "fvlb_step": ([_H, ctypes.c_long], ctypes.c_int),
@@ -353,6 +354,13 @@ class Simulation:
             raise FvlbError(r, last_error(self.h))
         return dict(mass=out[0], momentum=out[1:4].copy(), KE=out[4], PE=out[5],
                     nonfinite=int(out[6]), umax=out[7])
+
+    def conformation(self):
+        """Positive-definiteness check of A: nodes whose smallest eigenvalue
+        is not > 0, the smallest eigenvalue, the largest tr A."""
+        out = np.zeros(3)
+        check(lib.fvlb_conformation(self.h, _ptr(out)), self.h)
+        return dict(not_spd=int(out[0]), min_eig=out[1], max_trA=out[2])
 
     def state_size(self):
         n = ctypes.c_size_t()
