@@ -1584,13 +1584,19 @@ __global__ void __launch_bounds__(kReduceThreads)
        s += (long long)gridDim.x * blockDim.x) {
     double M[C];
     double tr = 0.0;
+    bool fin = true;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       double a = 0.0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) a += double(load_h<L, S>(h, P, s, k, i));
       M[k] = a;
+      fin &= isfinite(a);
       if (L::ca(k) == L::cb(k)) tr += 1.0 + a;
+    }
+    if (!fin) {             // (fmin in the eigenvalue routine would drop a NaN)
+      cnt += 1.0;
+      continue;
     }
     const double e = min_eigenvalue<L>(M);
     cnt += (e > 0.0) ? 0.0 : 1.0;
