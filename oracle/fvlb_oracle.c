@@ -18,7 +18,7 @@
  *
  * Lattice units: dx = dt = c = 1, c_s^2 = 1/3.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   R1  D3Q19 weights are not printed: 1/3, 1/18 (axis), 1/36 (diagonal).
  *   R2  grad u is a second-order central difference of the same-step
  *       velocity; at a node next to a halfway-bounce-back wall the one-sided
