@@ -210,6 +210,22 @@ int fvlb_init_fields(fvlb_t h, const double *u0, const double *p0,
  * waiting.  Each step evaluates the force at the current t, then t += 1. */
 int fvlb_step(fvlb_t h, long n);
 
+/* Periodic finiteness check (failure detection): every `every` steps
+ * fvlb_step enqueues the FP64 diagnostics of fvlb_reduce on the handle's
+ * stream and copies them to page-locked host memory behind an event; no
+ * call waits for it.  The result is collected by the next fvlb_step or
+ * fvlb_status: once a check has found a non-finite value, fvlb_step enqueues
+ * nothing more and returns FVLB_EUNSTABLE (the message names the step of the
+ * check) until fvlb_init_fields or fvlb_load_state installs a new state.  At
+ * most one check is in flight; a check point reached while the previous one
+ * is still running is skipped.  every = 0 (the default) turns it off.
+ * FVLB_EINVAL for every < 0. */
+int fvlb_set_check_interval(fvlb_t h, long every);
+
+/* Result of the periodic check: FVLB_OK, or FVLB_EUNSTABLE once a check has
+ * found a non-finite value.  wait != 0 first waits for a check in flight. */
+int fvlb_status(fvlb_t h, int wait);
+
 /* Copy one field of the current state into host_out (FP64, layouts above),
  * synchronising the handle's stream.  count is the number of doubles the
  * buffer holds; if it is smaller than N * components, FVLB_EINVAL is

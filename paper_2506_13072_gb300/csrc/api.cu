@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fvlb.h"
 #include "fvlb_internal.h"
 #include "fvlb_kernels.cuh"
@@ -73,6 +75,13 @@ struct fvlb_s {
   void* taup = nullptr;     // original scheme: polymer stress working array
   int model = FVLB_MODEL_OLDROYD_B;
   double mpar = 0.0;        // alpha (Giesekus) or eps (PTT)
+  // periodic finiteness check (fvlb_set_check_interval)
+  long chk_every = 0;       // steps between checks, 0: off
+  double* chk_host = nullptr;  // page-locked copy of the last check's diagnostics
+  cudaEvent_t chk_ev = nullptr;
+  bool chk_pending = false;
+  long long chk_t = 0;      // step count of the pending check
+  long long bad_t = -1;     // step count at which a check found non-finite values
   fvlb_alloc_fn alloc = nullptr;
   fvlb_free_fn free_ = nullptr;
   void* actx = nullptr;
@@ -81,6 +90,13 @@ struct fvlb_s {
 };
 
 namespace {
+
+// NVTX range over one API call (visible in a profiler timeline; near free
+// when no tool is attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 int fail(fvlb_t h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -334,6 +350,8 @@ cudaError_t reduce_finalize(const double* part, int nparts, long long N, double*
 // ===========================================================================
 extern "C" {
 
+static int check_poll(fvlb_t h, bool wait);
+
 int fvlb_set_allocator(fvlb_alloc_fn alloc_fn, fvlb_free_fn free_fn, void* ctx) {
   if ((alloc_fn == nullptr) != (free_fn == nullptr))
     return fail(nullptr, FVLB_EINVAL, "fvlb_set_allocator: give both hooks or neither");
@@ -472,14 +490,18 @@ int fvlb_set_stream(fvlb_t h, void* stream) {
 
 int fvlb_init_fields(fvlb_t h, const double* u0, const double* p0, const double* A0) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  Range range("fvlb_init_fields");
   int r = ensure_state(h, false);
   if (r != FVLB_OK) return r;
+  r = check_poll(h, true);   // a new state: earlier check results no longer apply
+  if (r != FVLB_OK) return r;
+  h->bad_t = -1;
   return run_init(h, u0, p0, A0);
 }
 
 // the original scheme's polymer stress array (C * pitch working-precision
 // values), allocated on first need through the allocator hooks
-int ensure_taup(fvlb_t h) {
+static int ensure_taup(fvlb_t h) {
   if (h->scheme != FVLB_SCHEME_ORIGINAL || h->taup) return FVLB_OK;
   const size_t rb = h->storage == FVLB_FP64 ? 8 : 4;
   h->taup = dev_alloc(h, rb * (size_t)h->C * (size_t)h->pitch);
@@ -487,13 +509,52 @@ int ensure_taup(fvlb_t h) {
   return FVLB_OK;
 }
 
+// The periodic finiteness check: collect the result of the pending check
+// (waiting for it if `wait`), recording the step of a failure.
+static int check_poll(fvlb_t h, bool wait) {
+  if (!h->chk_pending) return FVLB_OK;
+  cudaError_t e = wait ? cudaEventSynchronize(h->chk_ev) : cudaEventQuery(h->chk_ev);
+  if (e == cudaErrorNotReady) return FVLB_OK;
+  if (e != cudaSuccess) return cuda_fail(h, e, "finiteness check");
+  h->chk_pending = false;
+  if (h->chk_host[6] > 0 && h->bad_t < 0) h->bad_t = h->chk_t;
+  return FVLB_OK;
+}
+
+static int unstable_fail(fvlb_t h) {
+  return fail(h, FVLB_EUNSTABLE,
+              ("non-finite values in the state (periodic check at step " +
+               std::to_string(h->bad_t) + ")").c_str());
+}
+
+// Enqueue the diagnostics of the current state and a copy of them to
+// page-locked host memory, marked by an event (no host wait).
+static int check_enqueue(fvlb_t h) {
+  StepDesc d = make_desc(h);
+  cudaError_t e = h->lattice == FVLB_D2Q9 ? fvlb::reduce_d2q9(d, h->part, h->red)
+                                          : fvlb::reduce_d3q19(d, h->part, h->red);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->chk_host, h->red, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->chk_ev, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "finiteness check");
+  h->chk_pending = true;
+  h->chk_t = h->t;
+  return FVLB_OK;
+}
+
 int fvlb_step(fvlb_t h, long n) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (n < 0) return fail(h, FVLB_EINVAL, "fvlb_step: n must be >= 0");
+  Range range("fvlb_step");
   int r = ensure_state(h, true);
   if (r != FVLB_OK) return r;
   r = ensure_taup(h);
   if (r != FVLB_OK) return r;
+  if (h->chk_every) {
+    r = check_poll(h, false);
+    if (r != FVLB_OK) return r;
+    if (h->bad_t >= 0) return unstable_fail(h);
+  }
   for (long k = 0; k < n; ++k) {
     StepDesc d = make_desc(h);
     cudaError_t e = h->lattice == FVLB_D2Q9 ? fvlb::step_d2q9(d) : fvlb::step_d3q19(d);
@@ -501,12 +562,47 @@ int fvlb_step(fvlb_t h, long n) {
     h->cur = 1 - h->cur;
     h->first = 0;
     h->t += 1;
+    if (h->chk_every && h->t % h->chk_every == 0) {
+      r = check_poll(h, false);
+      if (r != FVLB_OK) return r;
+      if (h->bad_t >= 0) return unstable_fail(h);
+      if (!h->chk_pending) {   // one check in flight at a time
+        r = check_enqueue(h);
+        if (r != FVLB_OK) return r;
+      }
+    }
   }
+  return FVLB_OK;
+}
+
+int fvlb_set_check_interval(fvlb_t h, long every) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  if (every < 0) return fail(h, FVLB_EINVAL, "fvlb_set_check_interval: every must be >= 0");
+  if (every && !h->chk_host) {
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->chk_host), sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->chk_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_set_check_interval");
+  }
+  if (!every) {
+    int r = check_poll(h, true);
+    if (r != FVLB_OK) return r;
+  }
+  h->chk_every = every;
+  return FVLB_OK;
+}
+
+int fvlb_status(fvlb_t h, int wait) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  int r = check_poll(h, wait != 0);
+  if (r != FVLB_OK) return r;
+  if (h->bad_t >= 0) return unstable_fail(h);
   return FVLB_OK;
 }
 
 int fvlb_fields(fvlb_t h, int which, double* host_out, size_t count) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  Range range("fvlb_fields");
   const int nc = comps(h, which);
   if (nc == 0) return fail(h, FVLB_EINVAL, "fvlb_fields: unknown field");
   if (!host_out) return fail(h, FVLB_EINVAL, "fvlb_fields: host_out is NULL");
@@ -532,6 +628,7 @@ int fvlb_fields(fvlb_t h, int which, double* host_out, size_t count) {
 
 int fvlb_reduce(fvlb_t h, double out[8]) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  Range range("fvlb_reduce");
   if (!out) return fail(h, FVLB_EINVAL, "fvlb_reduce: out is NULL");
   int r = ensure_state(h, true);
   if (r != FVLB_OK) return r;
@@ -550,6 +647,7 @@ int fvlb_reduce(fvlb_t h, double out[8]) {
 
 int fvlb_conformation(fvlb_t h, double out[3]) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  Range range("fvlb_conformation");
   if (!out) return fail(h, FVLB_EINVAL, "fvlb_conformation: out is NULL");
   int r = ensure_state(h, true);
   if (r != FVLB_OK) return r;
@@ -650,6 +748,9 @@ int fvlb_load_state(fvlb_t h, const void* host_buf, size_t bytes) {
     return fail(h, FVLB_EINVAL, "fvlb_load_state: header does not match this handle");
   int r = ensure_state(h, false);
   if (r != FVLB_OK) return r;
+  r = check_poll(h, true);   // a new state: earlier check results no longer apply
+  if (r != FVLB_OK) return r;
+  h->bad_t = -1;
   const char* p = static_cast<const char*>(host_buf) + sizeof(hd);
   const size_t P = (size_t)h->pitch, sb = storage_bytes(h->storage);
   const size_t bf = sb * h->Q * P, bh = sb * (size_t)h->C * h->Q * P, bc = chi_bytes(h->storage) * h->C * P;
@@ -679,6 +780,8 @@ int fvlb_destroy(fvlb_t h) {
   if (!h) return FVLB_OK;
   cudaStreamSynchronize(h->stream);
   free_all(h);
+  if (h->chk_ev) cudaEventDestroy(h->chk_ev);
+  if (h->chk_host) cudaFreeHost(h->chk_host);
   delete h;
   return FVLB_OK;
 }

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fvlb.h"
 #include "fvlb_batch_impl.cuh"
 
@@ -468,6 +470,8 @@ int fvlb_batch_init_fields(fvlb_batch_t b, int index, const double* u0, const do
 }
 
 int fvlb_batch_step(fvlb_batch_t b, long n) {
+  nvtxRangePushA("fvlb_batch_step");   // one range over the whole call (graph replays)
+  struct Pop { ~Pop() { nvtxRangePop(); } } pop;
   if (!b) return set_global_error(FVLB_EINVAL, "NULL batch");
   if (n < 0) return bfail(b, FVLB_EINVAL, "fvlb_batch_step: n must be >= 0");
   int r = FVLB_OK;

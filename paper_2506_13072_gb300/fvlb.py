@@ -101,6 +101,8 @@ _SIGS = {
     "fvlb_set_scheme": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_model": ([_H, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "fvlb_conformation": ([_H, _dp], ctypes.c_int),
+    "fvlb_set_check_interval": ([_H, ctypes.c_long], ctypes.c_int),
+    "fvlb_status": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
     "fvlb_init_fields": ([_H, _dp, _dp, _dp], ctypes.c_int),
     "fvlb_step": ([_H, ctypes.c_long], ctypes.c_int),
@@ -292,6 +294,16 @@ class Simulation:
 
     def set_scheme(self, scheme):
         check(lib.fvlb_set_scheme(self.h, int(scheme)), self.h)
+
+    def set_check_interval(self, every):
+        """Check the state for non-finite values every `every` steps (0: off);
+        a failed check makes later steps raise FvlbError(FVLB_EUNSTABLE)."""
+        check(lib.fvlb_set_check_interval(self.h, int(every)), self.h)
+
+    def status(self, wait=False):
+        """FVLB_OK, or FVLB_EUNSTABLE once a periodic check found a non-finite
+        value (no exception)."""
+        return lib.fvlb_status(self.h, 1 if wait else 0)
 
     def set_model(self, model, mpar=0.0):
         check(lib.fvlb_set_model(self.h, int(model), float(mpar)), self.h)

@@ -51,6 +51,8 @@ def test_null_handle_calls_fail_cleanly():
     assert F.lib.fvlb_set_scheme(None, 1) == F.FVLB_EINVAL
     assert F.lib.fvlb_set_model(None, 1, 0.1) == F.FVLB_EINVAL
     assert F.lib.fvlb_conformation(None, None) == F.FVLB_EINVAL
+    assert F.lib.fvlb_set_check_interval(None, 5) == F.FVLB_EINVAL
+    assert F.lib.fvlb_status(None, 1) == F.FVLB_EINVAL
     assert F.lib.fvlb_destroy(None) == F.FVLB_OK
     assert isinstance(F.lib.fvlb_last_error(None), bytes)
 
