@@ -579,8 +579,7 @@ int fvlb_set_check_interval(fvlb_t h, long every) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (every < 0) return fail(h, FVLB_EINVAL, "fvlb_set_check_interval: every must be >= 0");
   if (every && !h->chk_host) {
-    cudaError_t e = cudaSetDevice(h->device);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->chk_host), sizeof(double) * 8);
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&h->chk_host), sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->chk_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_set_check_interval");
   }
