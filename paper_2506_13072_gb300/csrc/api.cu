@@ -578,9 +578,10 @@ int fvlb_step(fvlb_t h, long n) {
 int fvlb_set_check_interval(fvlb_t h, long every) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (every < 0) return fail(h, FVLB_EINVAL, "fvlb_set_check_interval: every must be >= 0");
-  if (every && !h->chk_host) {
-    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&h->chk_host), sizeof(double) * 8);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->chk_ev, cudaEventDisableTiming);
+  if (every) {
+    cudaError_t e = cudaSuccess;
+    if (!h->chk_host) e = cudaMallocHost(reinterpret_cast<void**>(&h->chk_host), sizeof(double) * 8);
+    if (e == cudaSuccess && !h->chk_ev) e = cudaEventCreateWithFlags(&h->chk_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_set_check_interval");
   }
   if (!every) {
