@@ -220,15 +220,16 @@ def test_full_size_d2q9_2048(prec):
     """2048^2 D2Q9, the grid and launch shape of the benchmark's D2Q9 forms."""
     small = W.four_roll(n=32, Wi=0.5, beta=0.5)
     _with_random(small, seed=6)
-    _tiled_check(small, 64, 12, prec, TOL[prec])
+    _tiled_check(small, 64, 12, prec, TOL[prec] if prec == FP32 else 2e-3)
 
 
 @pytest.mark.parametrize("prec", [FP16, BF16])
 def test_full_size_d3q19_256_16bit(prec):
-    """256^3 D3Q19 with 16-bit deviation storage (the benchmark's forms)."""
+    """256^3 D3Q19 with 16-bit deviation storage (the benchmark's forms);
+    bounds of the 16-bit Taylor-Green forms (u and tau_p together)."""
     small = W.Problem("t", W.D3Q19, 16, 16, 16, 0.52, 0.004, 800.0)
     _with_random(small, seed=5, U=0.02, dA=0.3)
-    _tiled_check(small, 16, 6, prec, TOL[prec])
+    _tiled_check(small, 16, 6, prec, 2e-3 if prec == FP16 else 1.5e-2)
 
 
 # ---------------------------------------------------------------------------
