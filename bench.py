@@ -306,6 +306,39 @@ def batch_rate(F, precision, stream, steps=40):
             "launches_per_step": 1}
 
 
+def one_by_one_rate(F, precision, stream, steps=10):
+    """The same 512 instances as batch_rate, each its own handle stepped by
+    its own fused launch through the public API (512 launches a step): the
+    baseline the batched form replaces."""
+    import torch
+
+    from paper_2506_13072_gb300 import workloads as W
+
+    probs = W.batch_instances(count=512, seed=0)
+    sims = [F.Simulation.from_problem(p, precision=precision, stream=stream) for p in probs]
+    for s in sims:
+        s.init_fields()
+        s.step(2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    sites = sum(p.sites for p in probs)
+    bpu = sims[0].bytes_per_update()
+    for s in sims:
+        s.close()
+    return {"mlups": round(sites * steps / dt / 1e6, 1),
+            "gbs_algorithmic": round(bpu * sites * steps / dt / 1e9, 1),
+            "bytes_per_update": bpu, "ms_per_step": round(1e3 * dt / steps, 4),
+            "sites": sites, "instances": 512, "launches_per_step": 512}
+
+
 def closure_rate(F, stream, steps=10):
     """D3Q19 Taylor-Green 256^3 FP32 with the learned closure: the network is
     trained on pairs from Taylor-Green 32^3 runs of the plain method (Wi 1 and
@@ -444,6 +477,10 @@ def run_ours(args, rank, world, dist):
         for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("fp32", F.FVLB_FP32)):
             forms[f"batched_512_d2q9_{name}"] = batch_rate(F, prec, stream)
             torch.cuda.empty_cache()
+        obo = one_by_one_rate(F, F.FVLB_FP32, stream)
+        obo["batched_fp32_speedup"] = round(forms["batched_512_d2q9_fp32"]["mlups"] / obo["mlups"], 2)
+        forms["d2q9_512_instances_fp32_one_by_one"] = obo
+        torch.cuda.empty_cache()
         # other constitutive models (relaxation part of chi): same bytes per update
         for name, model, par in (("giesekus", F.FVLB_MODEL_GIESEKUS, 0.3),
                                  ("ptt_exp", F.FVLB_MODEL_PTT_EXP, 0.25)):
