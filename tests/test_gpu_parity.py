@@ -301,6 +301,34 @@ def test_checkpoint_resume_bitwise(prec):
     b.close()
 
 
+@pytest.mark.parametrize("prec", [FP32, FP16])
+def test_deterministic_on_concurrent_streams(prec):
+    """No atomics and no order-dependent sums: two handles stepping the same
+    problem at once on two streams end in the same bytes as one handle on
+    the default stream."""
+    import torch
+
+    pr = W.taylor_green_3d(n=32, U0=0.02, Re=100, Wi=1.0, beta=0.5)
+    _with_random(pr, seed=8)
+    F = fvlb()
+    ref = gpu_sim(pr, prec)
+    ref.step(30)
+    want = ref.save_state()
+    ref.close()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    sims = []
+    for st in streams:
+        s = F.Simulation.from_problem(pr, precision=prec, stream=st)
+        s.init_fields(pr.u0, pr.p0, pr.A0)
+        sims.append(s)
+    for _ in range(30):
+        for s in sims:
+            s.step(1)
+    for s in sims:
+        assert np.array_equal(s.save_state(), want)
+        s.close()
+
+
 def test_fused_and_split_agree():
     pr = W.taylor_green_3d(n=40, U0=0.02, Re=100, Wi=1.0, beta=0.5)
     a = gpu_sim(pr, FP32, kernel=0)
