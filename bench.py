@@ -457,22 +457,27 @@ def run_ours(args, rank, world, dist):
         for name, prec in (("fp32", F.FVLB_FP32), ("fp16_dev", F.FVLB_FP16_DEV)):
             forms[f"d2q9_2048^2_four_roll_{name}"] = form_rate(F, pr2, prec, K, 2, stream)
         # The comparison of Tables 1-2: the present scheme against the original
-        # one (stress divergence by finite differences, three launches a step).
-        # Both are timed in the split form and the present one also fused.
+        # one (stress divergence by finite differences as a body force).  Each
+        # in the fused form (present: one launch; original: stress, its
+        # divergence and the fused step, three launches) and the split form
+        # (present: two launches; original: stress, velocity, collision).
         for key, p in (("d3q19_256^3_fp32", pr), ("d2q9_2048^2_four_roll_fp32", pr2)):
             split = form_rate(F, p, F.FVLB_FP32, K, 2, stream, kernel=1)
-            orig = form_rate(F, p, F.FVLB_FP32, K, 2, stream, kernel=1,
+            orig_split = form_rate(F, p, F.FVLB_FP32, K, 2, stream, kernel=1,
+                                   scheme=F.FVLB_SCHEME_ORIGINAL)
+            orig = form_rate(F, p, F.FVLB_FP32, K, 2, stream, kernel=0,
                              scheme=F.FVLB_SCHEME_ORIGINAL)
             fused_ms = (forms[key]["ms_per_step"] if key in forms        # D2Q9
                         else 1e3 * dt / args.steps if args.precision == "fp32"  # headline
                         else None)
-            orig["time_ratio_present_split_over_original"] = round(
-                split["ms_per_step"] / orig["ms_per_step"], 3)
+            orig_split["time_ratio_present_split_over_original_split"] = round(
+                split["ms_per_step"] / orig_split["ms_per_step"], 3)
             if fused_ms is not None:
-                orig["time_ratio_present_fused_over_original"] = round(
+                orig["time_ratio_present_fused_over_original_fused"] = round(
                     fused_ms / orig["ms_per_step"], 3)
             forms[f"{key}_split"] = split
             forms[f"{key}_original"] = orig
+            forms[f"{key}_original_split"] = orig_split
             torch.cuda.empty_cache()
         for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("fp32", F.FVLB_FP32)):
             forms[f"batched_512_d2q9_{name}"] = batch_rate(F, prec, stream)

@@ -173,9 +173,11 @@ int fvlb_set_kernel(fvlb_t h, int variant);
  * central differences (periodic wrap) and, next to a wall, by the one-sided
  * second-order difference through the two nodes inside, and it enters the
  * velocity, the Guo forcing term and the pressure as the body force does.
- * It runs as three launches per step (stress, velocity, collide-and-stream)
- * whatever the kernel variant; fvlb_fields and fvlb_reduce use the same
- * total force.  FVLB_EINVAL for an unknown scheme, for a walled axis of
+ * It runs as three launches per step: with FVLB_KERNEL_FUSED the stress,
+ * its divergence per node (a second working array of D x pitch values) and
+ * the fused step with that divergence in the body force and f^B off; with
+ * FVLB_KERNEL_SPLIT the stress, the velocity and the collide-and-stream
+ * kernel.  fvlb_fields and fvlb_reduce use the same total force.  FVLB_EINVAL for an unknown scheme, for a walled axis of
  * fewer than 3 nodes, or while a learned closure is attached. */
 int fvlb_set_scheme(fvlb_t h, int scheme);
 

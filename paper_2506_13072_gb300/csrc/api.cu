@@ -73,6 +73,7 @@ struct fvlb_s {
   unsigned long long* cl_count = nullptr;  // [0] network nodes, [1] fallbacks
   int scheme = FVLB_SCHEME_PRESENT;
   void* taup = nullptr;     // original scheme: polymer stress working array
+  void* fdiv = nullptr;     // original scheme: its divergence (fused variant)
   int model = FVLB_MODEL_OLDROYD_B;
   double mpar = 0.0;        // alpha (Giesekus) or eps (PTT)
   // periodic finiteness check (fvlb_set_check_interval)
@@ -138,6 +139,7 @@ void free_all(fvlb_t h) {
   h->part = h->red = h->fbuf = nullptr;
   h->cl_count = nullptr;
   h->taup = nullptr;
+  h->fdiv = nullptr;
   h->allocated = false;
 }
 
@@ -173,6 +175,7 @@ StepDesc make_desc(fvlb_t h) {
   d.cl_count = h->cl_count;
   d.scheme = h->scheme;
   d.taup = h->taup;
+  d.fdiv = h->fdiv;
   d.model = h->model;
   d.mpar = h->mpar;
   double c = 0.0;
@@ -500,12 +503,15 @@ int fvlb_init_fields(fvlb_t h, const double* u0, const double* p0, const double*
 }
 
 // the original scheme's polymer stress array (C * pitch working-precision
-// values), allocated on first need through the allocator hooks
+// values) and its divergence (D * pitch), allocated on first need through
+// the allocator hooks
 static int ensure_taup(fvlb_t h) {
-  if (h->scheme != FVLB_SCHEME_ORIGINAL || h->taup) return FVLB_OK;
+  if (h->scheme != FVLB_SCHEME_ORIGINAL) return FVLB_OK;
   const size_t rb = h->storage == FVLB_FP64 ? 8 : 4;
-  h->taup = dev_alloc(h, rb * (size_t)h->C * (size_t)h->pitch);
+  if (!h->taup) h->taup = dev_alloc(h, rb * (size_t)h->C * (size_t)h->pitch);
   if (!h->taup) return fail(h, FVLB_ENOMEM, "device allocation of the stress array failed");
+  if (!h->fdiv) h->fdiv = dev_alloc(h, rb * (size_t)h->D * (size_t)h->pitch);
+  if (!h->fdiv) return fail(h, FVLB_ENOMEM, "device allocation of the stress divergence failed");
   return FVLB_OK;
 }
 

@@ -36,6 +36,7 @@ struct StepDesc {
   unsigned long long* cl_count;  // [0] nodes on the network, [1] fallbacks
   int scheme;           // 0 present (f^B), 1 original (stress divergence as a force)
   void* taup;           // original scheme: C * pitch working-precision values
+  void* fdiv;           // original scheme, fused variant: D * pitch working-precision values
   int model;            // constitutive model (0 Oldroyd-B, 1 Giesekus, 2 / 3 PTT)
   double mpar;          // its parameter
 };

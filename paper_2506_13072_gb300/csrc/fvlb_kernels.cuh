@@ -505,6 +505,12 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     if (ok) {
       R F[3];
       body_force<L, R>(ph, gx, D == 3 ? gy : mm, F);
+      if (ph.fdiv) {  // the original scheme: + div tau_p of this node
+        const uint32_t sf = (D == 3) ? ((uint32_t)mm * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx
+                                     : (uint32_t)mm * (uint32_t)nx + (uint32_t)gx;
+#pragma unroll
+        for (int a = 0; a < D; ++a) F[a] += ph.fdiv[(uint32_t)a * P32 + sf];
+      }
       velocity<L, R>(fv, F, u);
     }
     Vel<R, D> t;
@@ -905,13 +911,17 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       }
       R F[3];
       body_force<L, R>(ph, xn, D == 3 ? y : m, F);
+      if (ph.fdiv) {  // the original scheme: + div tau_p of this node, no f^B
+#pragma unroll
+        for (int a = 0; a < D; ++a) F[a] += ph.fdiv[(uint32_t)a * P32 + sn32];
+      }
       R uu = R(0), Fu = R(0);
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         uu += u[a] * u[a];
         Fu += F[a] * u[a];
       }
-      const R kB = ph.eta_over_lam * ph.inv_tau_f;
+      const R kB = ph.fdiv ? R(0) : ph.eta_over_lam * ph.inv_tau_f;
       // pressure (Sec. 2.2, Appendix B)
       constexpr double w0 = L::w(0);
       const R fB0 = fB_dir<L, R>(0, Ad, kB);
@@ -1213,6 +1223,24 @@ __device__ __forceinline__ void div_taup(const Grid& g, const R* __restrict__ tp
       }
       dv[b] += d;
     }
+  }
+}
+
+// The original scheme ahead of the fused step: div tau_p of every node into
+// fdiv[a * pitch + s] (read by the fused step as part of the body force).
+template <class L, class S>
+__global__ void k_fdiv(Grid g, const RT<S>* __restrict__ taup, RT<S>* __restrict__ fdiv,
+                       long long N) {
+  using R = RT<S>;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(s % g.nx);
+    const int y = (int)((s / g.nx) % g.ny);
+    const int z = (int)(s / ((long long)g.nx * g.ny));
+    R dv[3];
+    div_taup<L, R>(g, taup, x, y, z, s, dv);
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) fdiv[a * g.pitch + s] = dv[a];
   }
 }
 

@@ -54,6 +54,7 @@ Phys<R> make_phys(const StepDesc& d) {
   p.cl_count = d.cl_count;
   p.model = d.model;
   p.mpar = R(d.mpar);
+  p.fdiv = nullptr;
   return p;
 }
 
@@ -135,16 +136,24 @@ cudaError_t step_impl(const StepDesc& d) {
             static_cast<const S*>(d.h_in), static_cast<S*>(d.h_out),
             static_cast<X*>(d.chi)};
   if (d.scheme == 1) {
-    // the original scheme: stress array, velocity with the stress divergence
-    // as a body force, collision without f^B (one thread per node each)
+    // the original scheme: the polymer stress of every node, then either its
+    // divergence per node and the fused step with it as part of the body
+    // force and f^B off (three launches), or the split velocity and
+    // collision kernels, which take the divergence themselves
     const int threads = 128;
     const int blocks = grid_stride_blocks(d.N, threads, d.sms);
-    R* ubuf = static_cast<R*>(d.ubuf);
     R* taup = static_cast<R*>(d.taup);
     k_taup<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, b.h_in, taup, d.N);
-    k_velocity<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, taup, d.N);
-    k_collide_split<L, S, true, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, taup, d.N);
-    return cudaGetLastError();
+    if (d.variant == 0 && !d.mlp) {
+      R* fdiv = static_cast<R*>(d.fdiv);
+      k_fdiv<L, S><<<blocks, threads, 0, d.stream>>>(g, taup, fdiv, d.N);
+      ph.fdiv = fdiv;
+    } else {
+      R* ubuf = static_cast<R*>(d.ubuf);
+      k_velocity<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, taup, d.N);
+      k_collide_split<L, S, true, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, taup, d.N);
+      return cudaGetLastError();
+    }
   }
   if (d.variant == 0) {
     // Shapes measured fastest on GB300 (256^3 D3Q19, 2048^2 D2Q9): 2D four

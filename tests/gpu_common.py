@@ -101,3 +101,21 @@ def tiled_problem(pr_small, reps):
     pr.p0 = np.tile(pr_small.p0, tile)
     pr.A0 = np.tile(pr_small.A0, tile + (1, 1))
     return pr
+
+
+def tiled_check(small, reps, steps, prec, tol, kernel=0, scheme=0):
+    """The GPU on `small` tiled `reps` times per axis against the oracle on
+    `small` (periodic problems only); asserts rel-L2 of u and tau_p <= tol."""
+    big = tiled_problem(small, reps)
+    s = gpu_sim(big, prec, kernel, scheme)
+    o = oracle_sim(small, scheme)
+    s.step(steps)
+    o.step(steps)
+    tile = (reps,) * small.D
+    ref_u = np.tile(o.u(), tile + (1,))
+    ref_t = np.tile(compact(o.tau_p()), tile + (1,))
+    eu = rel_l2(s.u(), ref_u, 1e-12)
+    et = rel_l2(s.tau_p(), ref_t, 1e-12)
+    s.close()
+    assert eu <= tol and et <= tol, (eu, et)
+    return eu, et

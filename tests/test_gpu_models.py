@@ -10,7 +10,7 @@ import pytest
 
 from paper_2506_13072_gb300 import workloads as W
 
-from gpu_common import compare, fvlb, tiled_problem
+from gpu_common import compare, fvlb, tiled_check
 
 pytestmark = pytest.mark.gpu
 
@@ -70,10 +70,11 @@ def test_models_ragged(lat, shape, walls, model, par, prec):
     compare(_with(pr, model, par), 30, prec, TOL[prec], chunks=2)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("model,par", MODELS)
-def test_models_original_scheme(model, par):
+def test_models_original_scheme(model, par, kernel):
     pr = _random(W.four_roll(n=32, Wi=1.0, beta=0.5), seed=43)
-    compare(_with(pr, model, par), 100, FP64, 1e-12, chunks=2, scheme=1)
+    compare(_with(pr, model, par), 100, FP64, 1e-12, kernel=kernel, chunks=2, scheme=1)
 
 
 @pytest.mark.parametrize("model,par", MODELS)
@@ -89,9 +90,9 @@ def test_models_full_size_launch_shapes(model, par):
     """1024^2 D2Q9 and 128^3 D3Q19 FP32 launch shapes, checked by periodic
     tiling of 32^2 and 16^3 oracle runs (every node compared)."""
     small = _with(_random(W.four_roll(n=32, Wi=1.0, beta=0.5), seed=44), model, par)
-    compare(tiled_problem(small, 32), 20, FP32, 1e-5, fields=("u", "tau_p"))
+    tiled_check(small, 32, 20, FP32, 1e-5)
     small3 = _with(_random(W.taylor_green_3d(n=16, Wi=1.0, beta=0.5), seed=45), model, par)
-    compare(tiled_problem(small3, 8), 10, FP32, 1e-5, fields=("u", "tau_p"))
+    tiled_check(small3, 8, 10, FP32, 1e-5)
 
 
 def test_model_validation():

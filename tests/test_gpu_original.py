@@ -22,29 +22,33 @@ def _random(pr, seed, U=0.02, dA=0.4):
     return pr
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_original_four_roll(prec):
+def test_original_four_roll(prec, kernel):
     pr = _random(W.four_roll(n=64, Wi=0.5, beta=0.5), seed=31, U=0.01, dA=0.3)
-    compare(pr, 200, prec, TOL[prec], chunks=2, scheme=ORIG)
+    compare(pr, 200, prec, TOL[prec], kernel=kernel, chunks=2, scheme=ORIG)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_original_poiseuille_walls(prec):
+def test_original_poiseuille_walls(prec, kernel):
     pr = W.poiseuille(L=32, nx=8, Wi=1.0, beta=0.1)
-    compare(pr, 400, prec, TOL[prec], chunks=2, scheme=ORIG)
+    compare(pr, 400, prec, TOL[prec], kernel=kernel, chunks=2, scheme=ORIG)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_original_taylor_green_3d(prec):
+def test_original_taylor_green_3d(prec, kernel):
     pr = W.taylor_green_3d(n=32, U0=0.02, Re=100, Wi=1.0, beta=0.5)
-    compare(pr, 40, prec, TOL[prec], chunks=2, scheme=ORIG)
+    compare(pr, 40, prec, TOL[prec], kernel=kernel, chunks=2, scheme=ORIG)
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("lat,shape,walls", [
     (W.D2Q9, (33, 17), 0b10), (W.D2Q9, (7, 5), 0b11),
     (W.D3Q19, (37, 19, 11), 0b100), (W.D3Q19, (5, 4, 6), 0b011)])
-def test_original_ragged(prec, lat, shape, walls):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_original_ragged(prec, lat, shape, walls, kernel):
     if lat == W.D2Q9:
         nx, ny = shape
         pr = W.Problem("r", W.D2Q9, nx, ny, 1, 0.7, 0.15, 11.0, W.FORCE_CONST,
@@ -54,7 +58,7 @@ def test_original_ragged(prec, lat, shape, walls):
         pr = W.Problem("r3", W.D3Q19, nx, ny, nz, 0.75, 0.1, 13.0, W.FORCE_CONST,
                        (1e-5, 2e-5, -1e-5), walls=walls)
     _random(pr, seed=sum(shape) + walls)
-    compare(pr, 30, prec, TOL[prec], chunks=2, scheme=ORIG)
+    compare(pr, 30, prec, TOL[prec], kernel=kernel, chunks=2, scheme=ORIG)
 
 
 def test_original_16bit_storage():
@@ -118,3 +122,16 @@ def test_scheme_validation():
         assert F.lib.fvlb_set_scheme(h, F.FVLB_SCHEME_PRESENT) == F.FVLB_OK
     finally:
         F.lib.fvlb_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP16])
+def test_original_full_size_launch_shapes(prec):
+    """The fused original scheme in the 256^3 D3Q19 and 2048^2 D2Q9 launch
+    shapes of the benchmark, by periodic tiling of 16^3 and 32^2 oracle runs."""
+    from gpu_common import tiled_check
+
+    tol = TOL[FP32] if prec == FP32 else 2e-3
+    small = _random(W.taylor_green_3d(n=16, Wi=1.0, beta=0.5), seed=35)
+    tiled_check(small, 16, 6, prec, tol, scheme=ORIG)
+    small2 = _random(W.four_roll(n=32, Wi=0.5, beta=0.5), seed=36)
+    tiled_check(small2, 64, 12, prec, tol, scheme=ORIG)
