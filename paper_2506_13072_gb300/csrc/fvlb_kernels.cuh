@@ -420,7 +420,8 @@ struct TileCfg {
 // One tile of the fused step: tile (bx, by) of the plane, chunk bz of the
 // march axis.  Called by k_step_fused (one tile per block) and by the
 // batched persistent kernel (many tiles of many grids per block).
-template <class L, class S, int GX, int TY, bool WALLS, bool FW, bool CL = false, int XN = 1>
+template <class L, class S, int GX, int TY, bool WALLS, bool FW, bool CL = false, int XN = 1,
+          bool ORIG = false>
 __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                                            const Bufs<S>& b, int mchunk, int bx, int by,
                                            int bz) {
@@ -505,7 +506,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     if (ok) {
       R F[3];
       body_force<L, R>(ph, gx, D == 3 ? gy : mm, F);
-      if (ph.fdiv) {  // the original scheme: + div tau_p of this node
+      if constexpr (ORIG) {  // the original scheme: + div tau_p of this node
         const uint32_t sf = (D == 3) ? ((uint32_t)mm * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx
                                      : (uint32_t)mm * (uint32_t)nx + (uint32_t)gx;
 #pragma unroll
@@ -911,7 +912,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       }
       R F[3];
       body_force<L, R>(ph, xn, D == 3 ? y : m, F);
-      if (ph.fdiv) {  // the original scheme: + div tau_p of this node, no f^B
+      if constexpr (ORIG) {  // the original scheme: + div tau_p of this node, no f^B
 #pragma unroll
         for (int a = 0; a < D; ++a) F[a] += ph.fdiv[(uint32_t)a * P32 + sn32];
       }
@@ -921,7 +922,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         uu += u[a] * u[a];
         Fu += F[a] * u[a];
       }
-      const R kB = ph.fdiv ? R(0) : ph.eta_over_lam * ph.inv_tau_f;
+      const R kB = ORIG ? R(0) : ph.eta_over_lam * ph.inv_tau_f;
       // pressure (Sec. 2.2, Appendix B)
       constexpr double w0 = L::w(0);
       const R fB0 = fB_dir<L, R>(0, Ad, kB);
@@ -1107,10 +1108,11 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 }
 
 template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL = false,
-          int XN = 1>
+          int XN = 1, bool ORIG = false>
 __global__ void __launch_bounds__(FusedShape<L, GX, TY, FW, XN>::NT, MINB)
     k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
-  fused_tile<L, S, GX, TY, WALLS, FW, CL, XN>(g, ph, b, mchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+  fused_tile<L, S, GX, TY, WALLS, FW, CL, XN, ORIG>(g, ph, b, mchunk, blockIdx.x, blockIdx.y,
+                                                    blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------

@@ -273,8 +273,8 @@ struct Phys {
   unsigned long long* cl_count;  // [0] nodes on the network, [1] fallbacks
   int model;          // constitutive model: 0 Oldroyd-B, 1 Giesekus, 2 / 3 PTT
   R mpar;             // its parameter: alpha (Giesekus) or eps (PTT)
-  const R* fdiv;      // fused step of the original scheme: div tau_p [D][pitch]
-                      // added to the body force, f^B off (null: the present scheme)
+  const R* fdiv;      // fused step of the original scheme: div tau_p [D][pitch],
+                      // added to the body force (null for the present scheme)
 };
 
 template <class S>

@@ -85,12 +85,13 @@ cudaError_t allow_dynamic_smem(K* kern, size_t bytes) {
 
 // Launch a fused-step kernel instance; a tile of more than 48 KB of shared
 // memory (XN > 1) is given it dynamically.
-template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL, int XN>
+template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL, int XN,
+          bool ORIG = false>
 cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                           const Bufs<S>& b, int mchunk) {
   constexpr int NT = FusedShape<L, GX, TY, FW, XN>::NT;
   constexpr size_t dyn = TileCfg<L, S, GX, TY, FW, CL, XN>::kDynamicBytes;
-  auto kern = k_step_fused<L, S, GX, TY, MINB, WALLS, FW, CL, XN>;
+  auto kern = k_step_fused<L, S, GX, TY, MINB, WALLS, FW, CL, XN, ORIG>;
   if constexpr (dyn > 0) {
     const cudaError_t e = allow_dynamic_smem(kern, dyn);
     if (e != cudaSuccess) return e;
@@ -99,7 +100,7 @@ cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phy
   return cudaGetLastError();
 }
 
-template <class L, class S, int GX, int TY, int MINB, bool FW, int XN = 1>
+template <class L, class S, int GX, int TY, int MINB, bool FW, int XN = 1, bool ORIG = false>
 cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                          const Bufs<S>& b) {
   constexpr int TXS = GX * 32 * XN;
@@ -116,14 +117,43 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   mchunk = std::min(mchunk, nm);
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
-  if constexpr (std::is_same<S, float>::value && XN == 1) {
+  if constexpr (std::is_same<S, float>::value && XN == 1 && !ORIG) {
     if (d.mlp) {  // learned closure (FP32 storage only); one block per SM
       if (d.walls) return launch_kernel<L, S, GX, TY, 1, true, FW, true, 1>(grid, d, g, ph, b, mchunk);
       return launch_kernel<L, S, GX, TY, 1, false, FW, true, 1>(grid, d, g, ph, b, mchunk);
     }
   }
-  if (d.walls) return launch_kernel<L, S, GX, TY, MINB, true, FW, false, XN>(grid, d, g, ph, b, mchunk);
-  return launch_kernel<L, S, GX, TY, MINB, false, FW, false, XN>(grid, d, g, ph, b, mchunk);
+  if (d.walls)
+    return launch_kernel<L, S, GX, TY, MINB, true, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk);
+  return launch_kernel<L, S, GX, TY, MINB, false, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk);
+}
+
+// The fused step in the shape measured fastest on GB300 (256^3 D3Q19, 2048^2
+// D2Q9): 2D four 32-node groups x 3 components (384 threads, 2 blocks per
+// SM); 3D FP32 a 64-node row, each of the 6 component warps taking its two
+// 32-node halves in turn, + 4 halo fill warps (320 threads, 2 blocks per SM;
+// a 64-register cap for 3 blocks per SM measured slower); 3D 16-bit, FP64
+// and the learned closure one 32-node row.  ORIG: the original scheme's
+// step (div tau_p from ph.fdiv in the body force, f^B off).
+template <class L, class S, bool ORIG>
+cudaError_t fused_step(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
+                       const Bufs<S>& b) {
+  constexpr bool wide = sizeof(RT<S>) == 8;
+  if constexpr (L::D == 2) {
+    // 4 groups x 3 components, ring filled by the collision threads
+    if constexpr (wide) return launch_fused<L, S, 4, 1, 1, false, 1, ORIG>(d, g, ph, b);
+    else return launch_fused<L, S, 4, 1, 2, false, 1, ORIG>(d, g, ph, b);
+  } else {
+    if constexpr (wide) return launch_fused<L, S, 1, 1, 1, true, 1, ORIG>(d, g, ph, b);
+    else if constexpr (sizeof(S) == 4) {
+      if constexpr (!ORIG) {
+        if (d.mlp) return launch_fused<L, S, 1, 1, 2, true, 1>(d, g, ph, b);
+      }
+      return launch_fused<L, S, 1, 1, 2, true, 2, ORIG>(d, g, ph, b);
+    } else {
+      return launch_fused<L, S, 1, 1, 2, true, 1, ORIG>(d, g, ph, b);
+    }
+  }
 }
 
 template <class L, class S>
@@ -144,38 +174,23 @@ cudaError_t step_impl(const StepDesc& d) {
     const int blocks = grid_stride_blocks(d.N, threads, d.sms);
     R* taup = static_cast<R*>(d.taup);
     k_taup<L, S><<<blocks, threads, 0, d.stream>>>(g, ph, b.h_in, taup, d.N);
-    if (d.variant == 0 && !d.mlp) {
-      R* fdiv = static_cast<R*>(d.fdiv);
-      k_fdiv<L, S><<<blocks, threads, 0, d.stream>>>(g, taup, fdiv, d.N);
-      ph.fdiv = fdiv;
-    } else {
-      R* ubuf = static_cast<R*>(d.ubuf);
-      k_velocity<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, taup, d.N);
-      k_collide_split<L, S, true, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, taup, d.N);
-      return cudaGetLastError();
-    }
-  }
-  if (d.variant == 0) {
-    // Shapes measured fastest on GB300 (256^3 D3Q19, 2048^2 D2Q9): 2D four
-    // 32-node groups x 3 components (384 threads, 2 blocks per SM); 3D FP32
-    // a 64-node row, each of the 6 component warps taking its two 32-node
-    // halves in turn, + 4 halo fill warps (320 threads, 2 blocks per SM; a
-    // 64-register cap for 3 blocks per SM measured slower); 3D 16-bit, FP64
-    // and the learned closure one 32-node row.
-    constexpr bool wide = sizeof(RT<S>) == 8;
-    if constexpr (L::D == 2) {
-      // 4 groups x 3 components, ring filled by the collision threads
-      if constexpr (wide) return launch_fused<L, S, 4, 1, 1, false>(d, g, ph, b);
-      else return launch_fused<L, S, 4, 1, 2, false>(d, g, ph, b);
-    } else {
-      if constexpr (wide) return launch_fused<L, S, 1, 1, 1, true>(d, g, ph, b);
-      else if constexpr (sizeof(S) == 4) {
-        if (d.mlp) return launch_fused<L, S, 1, 1, 2, true, 1>(d, g, ph, b);
-        return launch_fused<L, S, 1, 1, 2, true, 2>(d, g, ph, b);
-      } else {
-        return launch_fused<L, S, 1, 1, 2, true, 1>(d, g, ph, b);
+    if constexpr (sizeof(S) >= 4) {  // fused form for FP32 and FP64 storage
+      if (d.variant == 0 && !d.mlp) {
+        R* fdiv = static_cast<R*>(d.fdiv);
+        k_fdiv<L, S><<<blocks, threads, 0, d.stream>>>(g, taup, fdiv, d.N);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ph.fdiv = fdiv;
+        return fused_step<L, S, true>(d, g, ph, b);
       }
     }
+    R* ubuf = static_cast<R*>(d.ubuf);
+    k_velocity<L, S, true><<<blocks, threads, 0, d.stream>>>(g, ph, b.f_in, ubuf, taup, d.N);
+    k_collide_split<L, S, true, true><<<blocks, threads, 0, d.stream>>>(g, ph, b, ubuf, taup, d.N);
+    return cudaGetLastError();
+  }
+  if (d.variant == 0) {
+    return fused_step<L, S, false>(d, g, ph, b);
   } else {
     const int threads = 128;
     const int blocks = grid_stride_blocks(d.N, threads, d.sms);
