@@ -392,8 +392,10 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     pr = main_problem(args)
     prec = F.PRECISIONS[args.precision]
+    scheme = F.FVLB_SCHEME_ORIGINAL if args.scheme == "original" else F.FVLB_SCHEME_PRESENT
+    launches = 3 if scheme == F.FVLB_SCHEME_ORIGINAL else 1     # per step
     sim = F.Simulation.from_problem(pr, precision=prec, kernel=F.FVLB_KERNEL_FUSED,
-                                    stream=stream)
+                                    stream=stream, scheme=scheme)
     sim.init_fields(pr.u0, pr.p0, pr.A0)
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -416,7 +418,8 @@ def run_ours(args, rank, world, dist):
     achieved = bpu * sites / launch_s / 1e9    # GB/s, algorithmic bytes
     peaks, which = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    tr = traffic_record(f"{args.lattice}_{args.n or 'default'}_{args.precision}_fused")
+    tr = (traffic_record(f"{args.lattice}_{args.n or 'default'}_{args.precision}_fused")
+          if launches == 1 else None)
 
     # end to end through the public API, host buffers: upload of the initial
     # fields, K steps, download of the velocity field, all inside the region;
@@ -432,7 +435,7 @@ def run_ours(args, rank, world, dist):
     p0 = pinned(pr.p0 if pr.p0 is not None else np.zeros(pr.shape))
     A0 = pinned(F.full_to_compact(np.broadcast_to(np.eye(D), pr.shape + (D, D))))
     e2e_steps = args.steps
-    sim = F.Simulation.from_problem(pr, precision=prec, stream=stream)
+    sim = F.Simulation.from_problem(pr, precision=prec, stream=stream, scheme=scheme)
     sim.init_fields(u0, p0, A0)
     sim.step(2)
     out = torch.empty(sites * D, dtype=torch.float64, pin_memory=True).numpy()
@@ -447,7 +450,8 @@ def run_ours(args, rank, world, dist):
     d2h = out.nbytes / e2e_steps
 
     forms = {}
-    if not args.no_forms and rank == 0 and args.lattice == "d3q19" and not args.n:
+    if (not args.no_forms and rank == 0 and args.lattice == "d3q19" and not args.n
+            and launches == 1):
         K = max(5, min(args.steps, 20))
         for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("bf16_dev", F.FVLB_BF16_DEV),
                            ("fp64", F.FVLB_FP64)):
@@ -513,18 +517,21 @@ def run_ours(args, rank, world, dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.precision, "f32 (16-bit storage)"),
         "data": "synthetic (seeded Taylor-Green initial field of Sec. 3.4)",
-        "config": config_dict(args),
+        "config": config_dict(args, "" if launches == 1 else "original scheme"),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": tr["dram_bytes_per_launch"] if tr else None,
                      "algorithmic_bytes_per_launch": bpu * sites,
                      "bytes_per_update": bpu, "peak_source": f"{which} hbm_gbs (copy)",
-                     "kernel": kernel_label(args.lattice, args.precision)},
+                     "kernel": kernel_label(args.lattice, args.precision)
+                               + ("" if launches == 1 else
+                                  "; original scheme: k_taup + k_fdiv + this kernel "
+                                  "(ORIG) per step, state bytes over the step time")},
         "e2e": {"value": round(sites * e2e_steps / e2e_dt / 1e6, 1), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "fvlb_init_fields from pinned host memory + K steps + "
                         "fvlb_fields(U) to pinned host memory"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches,
         "clocks": clk.summary(),
         "diagnostics": {"KE": diag["KE"], "PE": diag["PE"], "nonfinite": diag["nonfinite"]},
         "forms": forms,
@@ -545,6 +552,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="grid nodes per axis (0: the default workload)")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp64", "fp32", "fp16_dev", "bf16_dev", "fp16_dev_sr", "bf16_dev_sr"])
+    ap.add_argument("--scheme", default="present", choices=["present", "original"],
+                    help="original: the comparison scheme of Tables 1-2 (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
