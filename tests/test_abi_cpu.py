@@ -89,3 +89,36 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], cwd=tmp_path, capture_output=True, text=True)
     assert r.returncode != 0
     assert "ImportError" in r.stderr and "not built" in r.stderr
+
+
+def test_plain_c_program_links_and_calls(tmp_path):
+    """The header is plain C (C99, -pedantic) and a C program links the
+    library directly, without Python, and gets the documented statuses from
+    calls that need no GPU."""
+    import os
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(F.LIB_PATH)
+    src = tmp_path / "t.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "fvlb.h"\n'
+        "int main(void) {\n"
+        "  if (fvlb_destroy(NULL) != FVLB_OK) return 1;\n"
+        "  if (fvlb_set_walls(NULL, 1u) != FVLB_EINVAL) return 2;\n"
+        "  if (fvlb_step(NULL, 1) != FVLB_EINVAL) return 3;\n"
+        "  if (fvlb_set_model(NULL, FVLB_MODEL_GIESEKUS, 0.1) != FVLB_EINVAL) return 4;\n"
+        "  const char *m = fvlb_last_error(NULL);\n"
+        "  if (!m || !m[0]) return 5;\n"
+        '  printf("ok\\n");\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "t"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    f"-I{os.path.join(root, 'include')}", str(src), "-o", str(exe),
+                    f"-L{libdir}", "-lfvlb", f"-Wl,-rpath,{libdir}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
