@@ -339,8 +339,8 @@ def one_by_one_rate(F, precision, stream, steps=10):
             "sites": sites, "instances": 512, "launches_per_step": 512}
 
 
-def closure_rate(F, stream, steps=10):
-    """D3Q19 Taylor-Green 256^3 FP32 with the learned closure: the network is
+def closure_rate(F, stream, steps=10, n=None):
+    """D3Q19 Taylor-Green 256^3 (or n^3) FP32 with the learned closure: the network is
     trained on pairs from Taylor-Green 32^3 runs of the plain method (Wi 1 and
     0.2; relative loss), then replaces chi where its per-node residual is
     within 1e-2."""
@@ -360,7 +360,7 @@ def closure_rate(F, stream, steps=10):
     net.set_loss(1e-3)
     for n, b, lr in ((10000, 1024, 2e-3), (10000, 2048, 5e-4), (10000, 4096, 1e-4)):
         net.train(n, batch=b, lr=lr)
-    pr = tgv_problem(WORKLOAD["n"])
+    pr = tgv_problem(n or WORKLOAD["n"])
     sim = F.Simulation.from_problem(pr, precision=F.FVLB_FP32, stream=stream)
     sim.init_fields(pr.u0, pr.p0, pr.A0)
     sim.set_closure(net, tol=1e-2)
@@ -377,6 +377,27 @@ def closure_rate(F, stream, steps=10):
             "bytes_per_update": bpu, "ms_per_step": round(1e3 * dt / steps, 4),
             "network_share_of_node_updates": round(st["network"] / max(1, tot), 4),
             "tol": 1e-2}
+
+
+def run_form(args):
+    """One form alone (single GPU): the batched grids or the learned closure."""
+    import torch
+
+    from paper_2506_13072_gb300 import fvlb as F
+
+    torch.cuda.set_device(0)
+    F.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    if args.form.startswith("batched"):
+        prec = F.FVLB_FP32 if args.form == "batched_fp32" else F.FVLB_FP16_DEV
+        r = batch_rate(F, prec, stream, steps=args.steps)
+        work = "512 uneven D2Q9 grids (n log-uniform in [32, 512]), one launch per step"
+    else:
+        r = closure_rate(F, stream, steps=args.steps, n=args.n or None)
+        work = f"D3Q19 Taylor-Green {args.n or WORKLOAD['n']}^3 FP32 with the learned closure"
+    peaks, _ = measured_peaks()
+    r["frac_of_hbm_peak"] = round(r["gbs_algorithmic"] / float(peaks.get("hbm_gbs", 6800.0)), 3)
+    print(json.dumps({"form": args.form, "workload": work, "unit": UNIT, **r}), flush=True)
 
 
 def run_ours(args, rank, world, dist):
@@ -554,6 +575,8 @@ def main():
                     choices=["fp64", "fp32", "fp16_dev", "bf16_dev", "fp16_dev_sr", "bf16_dev_sr"])
     ap.add_argument("--scheme", default="present", choices=["present", "original"],
                     help="original: the comparison scheme of Tables 1-2 (profiling)")
+    ap.add_argument("--form", default="", choices=["", "batched_fp32", "batched_fp16", "closure"],
+                    help="time only this form and print its line (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -562,6 +585,9 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.form:
+        run_form(args)
         return
     if world > 1:
         import torch
