@@ -1025,12 +1025,14 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         j = i;
         return (uint32_t)d;
       };
-      // Without walls, a warp whose row and plane wrap around no periodic
-      // boundary (all but the first and last rows and planes) finds the
-      // destination of direction i at the fixed distance
-      // i * pitch + c_x + c_y nx (+ c_z nx ny) from its node, plus nx or
-      // -nx for the lanes at the two ends of a row.
-      const bool fast = !WALLS && (D == 2 || (y > 0 && y < ny - 1)) && m > 0 && m < nm - 1;
+      // A warp whose row and plane are neither the first nor the last (so
+      // that no population crosses a periodic wrap or a wall in y or along
+      // the march axis) finds the destination of direction i at the fixed
+      // distance i * pitch + c_x + c_y nx (+ c_z nx ny) from its node, plus
+      // nx or -nx for the lanes at the two ends of a periodic row; with walls
+      // on x the row ends bounce back, so those grids take the general rule.
+      const bool fast = (!WALLS || !(g.walls & 1)) && (D == 2 || (y > 0 && y < ny - 1)) &&
+                        m > 0 && m < nm - 1;
 
       // h_k: h* = (1 - 1/tau_h) h + w_i [alpha + c_i.u beta] with
       // alpha = (A-I)_k / tau_h + src and beta = 3 (A_k / tau_h + kh src)
