@@ -298,8 +298,10 @@ int fvlb_reduce_noalloc(int lattice, int storage, int nx, int ny, int nz,
  * object, advanced by ONE persistent kernel launch per step (each resident
  * block walks a fixed list of tiles of all grids), the steps replayed from a
  * captured CUDA graph.  The update of every node is the one of fvlb_step
- * (Sec. 2.2-2.3); the arithmetic does not depend on the tile shape, which an
- * autotuner picks by timing candidate shapes on the batch itself.
+ * (Sec. 2.2-2.3) with the paper's scheme and the Oldroyd-B model (no scheme,
+ * model or closure setting per instance); the arithmetic does not depend on
+ * the tile shape, which an autotuner picks by timing candidate shapes on the
+ * batch itself.
  * ------------------------------------------------------------------------- */
 typedef struct fvlb_batch_s *fvlb_batch_t;
 
