@@ -3,13 +3,23 @@
 Default workload: D3Q19 Taylor-Green vortex, 256^3 periodic, Re = 100,
 Wi = 1, beta = 0.5, u0 = 0.02, FP32 storage and arithmetic, fused kernel.
 One step = one fused collide-stream-stress launch over all 16.8 M sites.
-The state (18 GB) is far larger than L2, so no L2 flush is needed.
+The state (18.7 GB) is far larger than L2, so no L2 flush is needed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --forms          # every other form, one subprocess each
+    python bench.py --form NAME      # one form alone
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an
+The default run prints one JSON line (rank 0): the headline, its roofline,
+the end-to-end figure through the public API with page-locked host buffers,
+and the CPU oracle timed on the host cores (one core, and all cores as
+independent processes).  With N > 1 (torchrun) every rank runs an
 independent replica of the workload on its own GPU (the method's single
 grid does not shard here) and `value` counts the updates of all ranks.
+
+The other forms (precisions, the D2Q9 four-roll mill, the split kernels,
+the original scheme, other constitutive models, the batched grids and the
+learned closure) run only under --forms, each in a process of its own, so
+that one form's memory or failure cannot touch the headline.
 """
 from __future__ import annotations
 
@@ -18,8 +28,10 @@ import hashlib
 import json
 import math
 import os
+import resource
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -40,6 +52,16 @@ def kernel_hash() -> str:
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def maxrss_mb() -> float:
+    """Peak resident host memory of this process so far (MB)."""
+    return round(resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 1024.0, 1)
+
+
+def log(msg: str):
+    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg} (maxrss {maxrss_mb()} MB)\n")
+    sys.stderr.flush()
 
 
 def measured_peaks():
@@ -65,26 +87,39 @@ def traffic_record(kernel_key: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons, each sample stamped with the
+    host's monotonic clock when it arrives, so that the samples of a window
+    (the timed region) can be picked out afterwards."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, period_ms: int = 50):
         self.dev = device_index
+        self.period = period_ms
         self.proc = None
-        self.path = os.path.join("/tmp", f"fvlb_clocks_{os.getpid()}.csv")
+        self.rows = []
+        self.thread = None
 
     def __enter__(self):
         try:
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    self.rows.append((time.monotonic(), parts))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
         return self
 
     def __exit__(self, *a):
@@ -94,21 +129,24 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-            self.fh.close()
+            if self.thread is not None:
+                self.thread.join(timeout=5)
 
-    def summary(self):
+    def wait_for_samples(self, n: int, step_fn, limit_s: float = 4.0) -> int:
+        """Run step_fn() until n samples have arrived (at most limit_s);
+        returns how many times it ran."""
+        calls = 0
+        t0 = time.monotonic()
+        while (self.proc is not None and len(self.rows) < n
+               and time.monotonic() - t0 < limit_s):
+            step_fn()
+            calls += 1
+        return calls
+
+    def summary(self, t0: float, t1: float):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        with open(self.path) as fh:
-            for line in fh:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        try:
-            os.remove(self.path)
-        except OSError:
-            pass
+        rows = [r for (t, r) in self.rows if t0 <= t <= t1]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
 
@@ -128,30 +166,32 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None}
 
 
-def tgv_problem(n):
+def tgv_problem(n, fields=True, out_u=None, out_p=None):
     from paper_2506_13072_gb300 import workloads as W
 
     w = WORKLOAD
-    return W.taylor_green_3d(n=n, U0=w["U0"], Re=w["Re"], Wi=w["Wi"], beta=w["beta"])
+    return W.taylor_green_3d(n=n, U0=w["U0"], Re=w["Re"], Wi=w["Wi"], beta=w["beta"],
+                             fields=fields, out_u=out_u, out_p=out_p)
 
 
-def main_problem(args):
+def main_problem(args, fields=True):
     """The timed workload: the default D3Q19 Taylor-Green box, or (for
-    profiling and other forms) another size or the D2Q9 four-roll mill."""
+    profiling) another size or the D2Q9 four-roll mill (at rest)."""
     from paper_2506_13072_gb300 import workloads as W
 
     if args.lattice == "d2q9":
         return W.four_roll(n=args.n or 2048, Wi=0.5, beta=0.5)
-    return tgv_problem(args.n or WORKLOAD["n"])
+    return tgv_problem(args.n or WORKLOAD["n"], fields=fields)
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle, timed on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 
-def oracle_rate(seconds: float = 12.0, n: int = 32):
-    """The FP64 oracle (single thread) on a 32^3 Taylor-Green box with the
-    same physics; returns (MLUPS, steps, sites)."""
+def _oracle_worker(seconds: float, n: int):
+    """One single-threaded FP64 oracle on an n^3 Taylor-Green box with the
+    workload's physics, stepped for about `seconds`; returns (steps, sites,
+    elapsed)."""
     import oracle as O
 
     pr = tgv_problem(n)
@@ -163,8 +203,39 @@ def oracle_rate(seconds: float = 12.0, n: int = 32):
     while time.perf_counter() - t0 < seconds:
         o.step(1)
         steps += 1
-    dt = time.perf_counter() - t0
-    return pr.sites * steps / dt / 1e6, steps, pr.sites
+    return steps, pr.sites, time.perf_counter() - t0
+
+
+def cpu_baseline(seconds: float = 8.0, n: int = 32):
+    """The oracle as it stands, on the host cores: one process alone, then
+    one independent process per core at once (the oracle is single-threaded;
+    the processes are started with `spawn`, never forked from this CUDA
+    process).  Returns the cpu_baseline object (value = all cores)."""
+    import multiprocessing as mp
+
+    import oracle as O
+
+    O.build()
+    steps1, sites, dt1 = _oracle_worker(seconds, n)
+    one = sites * steps1 / dt1 / 1e6
+    cores = os.cpu_count() or 1
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            res = pool.starmap(_oracle_worker, [(seconds, n)] * cores)
+        allc = sum(s * m / t for (s, m, t) in res) / 1e6
+        used = cores
+        note = (f"{cores} independent single-threaded oracle processes at once, "
+                f"each on its own {n}^3 box for ~{seconds:g} s "
+                f"({sum(r[0] for r in res)} steps in all)")
+    except Exception as e:          # a host that cannot spawn: report the one-core figure
+        allc, used = one, 1
+        note = f"all-core leg failed ({type(e).__name__}); single process only"
+    return {"value": round(allc, 3), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"FP64 CPU oracle (plain C, gcc -O2), D3Q19 Taylor-Green {n}^3 "
+                      f"({sites} sites, the workload's Re, Wi, beta): {note}",
+            "single_core": {"value": round(one, 4), "unit": UNIT, "cores": 1,
+                            "sample": f"one process, {steps1} steps in {dt1:.1f} s"}}
 
 
 def run_reference(args, rank, world):
@@ -225,7 +296,7 @@ def config_dict(args=None, note=""):
     return {"workload": f"D3Q19 Taylor-Green vortex {n}^3 periodic, Re={w['Re']:g}, "
                         f"Wi={w['Wi']:g}, beta={w['beta']:g}, u0={w['U0']:g}, {prec} fused step",
             "lattice": w["lattice"], "grid": [n] * 3, "precision": prec,
-            "kernel": "fused", "l2": "state 18 GB >> 129 MB L2; no flush needed",
+            "kernel": "fused", "l2": "state 18.7 GB >> 129 MB L2; no flush needed",
             "parallelism": "replicas", "note": note}
 
 
@@ -260,12 +331,169 @@ def time_steps(sim, steps, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
+def pinned_f64(shape):
+    """A page-locked host float64 array (torch's pinned host allocator)."""
+    import torch
+
+    n = 1
+    for s in shape:
+        n *= s
+    return torch.empty(n, dtype=torch.float64, pin_memory=True).numpy().reshape(shape)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2506_13072_gb300 import fvlb as F
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    F.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    prec = F.PRECISIONS[args.precision]
+    scheme = F.FVLB_SCHEME_ORIGINAL if args.scheme == "original" else F.FVLB_SCHEME_PRESENT
+    launches = 3 if scheme == F.FVLB_SCHEME_ORIGINAL else 1     # per step
+
+    # The initial fields live in page-locked host buffers, written in place
+    # by the workload generator; the same buffers feed the end-to-end leg.
+    pr = main_problem(args, fields=False)
+    u0 = pinned_f64(pr.shape + (pr.D,))
+    p0 = pinned_f64(pr.shape)
+
+    def fill_inputs():
+        if args.lattice == "d3q19":
+            tgv_problem(pr.nx, out_u=u0, out_p=p0)
+        else:
+            u0[...] = 0.0           # the four-roll mill starts at rest
+            p0[...] = 0.0
+
+    fill_inputs()
+    log("fields built")
+    sim = F.Simulation.from_problem(pr, precision=prec, kernel=F.FVLB_KERNEL_FUSED,
+                                    stream=stream, scheme=scheme)
+    sim.init_fields(u0, p0, None)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    log("warm")
+
+    sites = pr.sites
+    with ClockSampler(local) as clk:
+        # more identical untimed steps until the clock sampler is reporting,
+        # so that its samples cover the timed region and the steps just before
+        preroll = clk.wait_for_samples(2, lambda: (sim.step(10), torch.cuda.synchronize()))
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.monotonic()
+        dt = time_steps(sim, args.steps, stream)
+        torch.cuda.synchronize()
+        w1 = time.monotonic()
+        time.sleep(0.06)
+    clocks = clk.summary(min(w0, w1 - 0.3), w1 + 0.02)
+    clocks["window"] = "timed region and the identical steps just before it"
+    dt, units = aggregate(dt, sites * args.steps, dist)
+    if dist is not None:
+        dist.barrier()
+    log(f"timed {args.steps} steps: {1e3 * dt / args.steps:.3f} ms/step")
+    diag = sim.reduce(check_finite=False)
+    bpu = sim.bytes_per_update()
+
+    # End to end through the public API with host buffers: upload of the
+    # initial fields (u, p; A = I is the library's rest default), K steps,
+    # download of the velocity field, all inside the timed region.  The same
+    # handle and page-locked buffers as above; the velocity is read back into
+    # the u buffer (the upload has completed when fvlb_init_fields returns).
+    sim.fields(F.FVLB_FIELD_U, u0.reshape(-1))      # first call allocates its buffer
+    fill_inputs()
+    sim.init_fields(u0, p0, None)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    sim.init_fields(u0, p0, None)
+    sim.step(args.steps)
+    sim.fields(F.FVLB_FIELD_U, u0.reshape(-1))
+    e2e_dt = time.perf_counter() - t0
+    sim.close()
+    e2e_dt, e2e_units = aggregate(e2e_dt, sites * args.steps, dist)
+    h2d = (u0.nbytes + p0.nbytes) / args.steps
+    d2h = u0.nbytes / args.steps
+    log("end to end done")
+
+    value = units / dt / 1e6
+    launch_s = dt / args.steps                 # one fused launch per step
+    achieved = bpu * sites / launch_s / 1e9    # GB/s, algorithmic bytes
+    peaks, which = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    tr = (traffic_record(f"{args.lattice}_{args.n or 'default'}_{args.precision}_fused")
+          if launches == 1 else None)
+
+    if rank != 0:
+        return
+    del u0, p0
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+        log("cpu baseline done")
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.precision, "f32 (16-bit storage)"),
+        "data": "synthetic (seeded Taylor-Green initial field of Sec. 3.4)",
+        "config": config_dict(args, "" if launches == 1 else "original scheme"),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                     "algorithmic_bytes_per_launch": bpu * sites,
+                     "bytes_per_update": bpu, "peak_source": f"{which} hbm_gbs (copy)",
+                     "kernel": kernel_label(args.lattice, args.precision)
+                               + ("" if launches == 1 else
+                                  "; original scheme: k_taup + k_fdiv + this kernel "
+                                  "(ORIG) per step, state bytes over the step time")},
+        "e2e": {"value": round(e2e_units / e2e_dt / 1e6, 1), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "fvlb_init_fields(u, p) from page-locked host memory + K steps + "
+                        "fvlb_fields(U) to page-locked host memory, one handle"},
+        "gpu_launches": args.steps * launches,
+        "clocks": clocks,
+        "preroll_steps": 10 * preroll,
+        "diagnostics": {"KE": diag["KE"], "PE": diag["PE"], "nonfinite": diag["nonfinite"]},
+        "host_maxrss_mb": maxrss_mb(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# The other forms (--forms / --form NAME), each in a process of its own
+# ---------------------------------------------------------------------------
+
+# name -> (lattice, n, precision, kernel, scheme, model, model parameter)
+FORMS = {
+    "d3q19_256_fp16_dev": ("d3q19", 256, "fp16_dev", 0, 0, 0, 0.0),
+    "d3q19_256_bf16_dev": ("d3q19", 256, "bf16_dev", 0, 0, 0, 0.0),
+    "d3q19_256_fp64": ("d3q19", 256, "fp64", 0, 0, 0, 0.0),
+    "d3q19_256_fp32_split": ("d3q19", 256, "fp32", 1, 0, 0, 0.0),
+    "d3q19_256_fp32_original": ("d3q19", 256, "fp32", 0, 1, 0, 0.0),
+    "d3q19_256_fp32_original_split": ("d3q19", 256, "fp32", 1, 1, 0, 0.0),
+    "d3q19_256_fp32_giesekus": ("d3q19", 256, "fp32", 0, 0, 1, 0.3),
+    "d3q19_256_fp32_ptt_exp": ("d3q19", 256, "fp32", 0, 0, 3, 0.25),
+    "d2q9_2048_fp32": ("d2q9", 2048, "fp32", 0, 0, 0, 0.0),
+    "d2q9_2048_fp16_dev": ("d2q9", 2048, "fp16_dev", 0, 0, 0, 0.0),
+    "d2q9_2048_fp32_split": ("d2q9", 2048, "fp32", 1, 0, 0, 0.0),
+    "d2q9_2048_fp32_original": ("d2q9", 2048, "fp32", 0, 1, 0, 0.0),
+    "d2q9_2048_fp32_original_split": ("d2q9", 2048, "fp32", 1, 1, 0, 0.0),
+}
+SPECIAL_FORMS = ["batched_fp32", "batched_fp16", "one_by_one_fp32", "closure"]
+
+
 def form_rate(F, pr, precision, steps, warmup, stream, kernel=0, scheme=0):
     import torch
 
     s = F.Simulation.from_problem(pr, precision=precision, kernel=kernel, stream=stream,
                                   scheme=scheme)
-    s.init_fields(pr.u0, pr.p0, pr.A0)
+    s.init_fields(pr.u0, pr.p0, None)
     s.step(warmup)
     torch.cuda.synchronize()
     dt = time_steps(s, steps, stream)
@@ -358,11 +586,12 @@ def closure_rate(F, stream, steps=10, n=None):
             net.collect(s, stride=5)
         s.close()
     net.set_loss(1e-3)
-    for n, b, lr in ((10000, 1024, 2e-3), (10000, 2048, 5e-4), (10000, 4096, 1e-4)):
-        net.train(n, batch=b, lr=lr)
+    for nt, b, lr in ((10000, 1024, 2e-3), (10000, 2048, 5e-4), (10000, 4096, 1e-4)):
+        net.train(nt, batch=b, lr=lr)
     pr = tgv_problem(n or WORKLOAD["n"])
     sim = F.Simulation.from_problem(pr, precision=F.FVLB_FP32, stream=stream)
-    sim.init_fields(pr.u0, pr.p0, pr.A0)
+    sim.init_fields(pr.u0, pr.p0, None)
+    pr.u0 = pr.p0 = None
     sim.set_closure(net, tol=1e-2)
     sim.step(3)
     torch.cuda.synchronize()
@@ -380,185 +609,65 @@ def closure_rate(F, stream, steps=10, n=None):
 
 
 def run_form(args):
-    """One form alone (single GPU): the batched grids or the learned closure."""
-    import torch
-
-    from paper_2506_13072_gb300 import fvlb as F
-
-    torch.cuda.set_device(0)
-    F.use_torch_allocator()
-    stream = torch.cuda.current_stream()
-    if args.form.startswith("batched"):
-        prec = F.FVLB_FP32 if args.form == "batched_fp32" else F.FVLB_FP16_DEV
-        r = batch_rate(F, prec, stream, steps=args.steps)
-        work = "512 uneven D2Q9 grids (n log-uniform in [32, 512]), one launch per step"
-    else:
-        r = closure_rate(F, stream, steps=args.steps, n=args.n or None)
-        work = f"D3Q19 Taylor-Green {args.n or WORKLOAD['n']}^3 FP32 with the learned closure"
-    peaks, _ = measured_peaks()
-    r["frac_of_hbm_peak"] = round(r["gbs_algorithmic"] / float(peaks.get("hbm_gbs", 6800.0)), 3)
-    print(json.dumps({"form": args.form, "workload": work, "unit": UNIT, **r}), flush=True)
-
-
-def run_ours(args, rank, world, dist):
-    import numpy as np
+    """One form alone (single GPU); prints its JSON line."""
     import torch
 
     from paper_2506_13072_gb300 import fvlb as F
     from paper_2506_13072_gb300 import workloads as W
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(0)
     F.use_torch_allocator()
     stream = torch.cuda.current_stream()
-    pr = main_problem(args)
-    prec = F.PRECISIONS[args.precision]
-    scheme = F.FVLB_SCHEME_ORIGINAL if args.scheme == "original" else F.FVLB_SCHEME_PRESENT
-    launches = 3 if scheme == F.FVLB_SCHEME_ORIGINAL else 1     # per step
-    sim = F.Simulation.from_problem(pr, precision=prec, kernel=F.FVLB_KERNEL_FUSED,
-                                    stream=stream, scheme=scheme)
-    sim.init_fields(pr.u0, pr.p0, pr.A0)
-    sim.step(args.warmup)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        dt = time_steps(sim, args.steps, stream)
-    torch.cuda.synchronize()
-    dt, units = aggregate(dt, pr.sites * args.steps, dist)
-    if dist is not None:
-        dist.barrier()
-    diag = sim.reduce(check_finite=False)
-    bpu = sim.bytes_per_update()
-    sim.close()
-
-    sites = pr.sites
-    value = units / dt / 1e6
-    launch_s = dt / args.steps                 # one fused launch per step
-    achieved = bpu * sites / launch_s / 1e9    # GB/s, algorithmic bytes
+    name = args.form
+    steps = max(5, args.steps)
+    if name in FORMS:
+        lat, n, precision, kernel, scheme, model, mpar = FORMS[name]
+        n = args.n or n
+        if lat == "d3q19":
+            pr = tgv_problem(n)
+            work = f"D3Q19 Taylor-Green {n}^3 (Re 100, Wi 1, beta 0.5)"
+        else:
+            pr = W.four_roll(n=n, Wi=0.5, beta=0.5)
+            work = f"D2Q9 four-roll mill {n}^2 (Wi 0.5, beta 0.5)"
+        pr.model, pr.mpar = model, mpar
+        work += (f", {precision}, {'split' if kernel else 'fused'} kernel, "
+                 f"{'original' if scheme else 'present'} scheme"
+                 + (f", model {model} ({mpar:g})" if model else ""))
+        r = form_rate(F, pr, F.PRECISIONS[precision], steps, 3, stream, kernel=kernel,
+                      scheme=scheme)
+    elif name.startswith("batched"):
+        prec = F.FVLB_FP32 if name == "batched_fp32" else F.FVLB_FP16_DEV
+        r = batch_rate(F, prec, stream, steps=max(steps, 40))
+        work = "512 uneven D2Q9 grids (n log-uniform in [32, 512]), one launch per step"
+    elif name == "one_by_one_fp32":
+        r = one_by_one_rate(F, F.FVLB_FP32, stream, steps=10)
+        work = "the same 512 D2Q9 grids, one handle and one fused launch each per step"
+    else:
+        r = closure_rate(F, stream, steps=steps, n=args.n or None)
+        work = f"D3Q19 Taylor-Green {args.n or WORKLOAD['n']}^3 FP32 with the learned closure"
     peaks, which = measured_peaks()
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    tr = (traffic_record(f"{args.lattice}_{args.n or 'default'}_{args.precision}_fused")
-          if launches == 1 else None)
+    r["frac_of_hbm_peak"] = round(r["gbs_algorithmic"] / float(peaks.get("hbm_gbs", 6800.0)), 3)
+    r["peak_source"] = f"{which} hbm_gbs (copy)"
+    print(json.dumps({"form": name, "workload": work, "unit": UNIT, **r,
+                      "host_maxrss_mb": maxrss_mb()}), flush=True)
 
-    # end to end through the public API, host buffers: upload of the initial
-    # fields, K steps, download of the velocity field, all inside the region;
-    # the host buffers are page-locked (pinned), as a serving process holds them
-    D = pr.D
 
-    def pinned(a):
-        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
-        t.numpy()[...] = a
-        return t.numpy()
-
-    u0 = pinned(pr.u0 if pr.u0 is not None else np.zeros(pr.shape + (D,)))
-    p0 = pinned(pr.p0 if pr.p0 is not None else np.zeros(pr.shape))
-    A0 = pinned(F.full_to_compact(np.broadcast_to(np.eye(D), pr.shape + (D, D))))
-    e2e_steps = args.steps
-    sim = F.Simulation.from_problem(pr, precision=prec, stream=stream, scheme=scheme)
-    sim.init_fields(u0, p0, A0)
-    sim.step(2)
-    out = torch.empty(sites * D, dtype=torch.float64, pin_memory=True).numpy()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sim.init_fields(u0, p0, A0)
-    sim.step(e2e_steps)
-    sim.fields(F.FVLB_FIELD_U, out)
-    e2e_dt = time.perf_counter() - t0
-    sim.close()
-    h2d = (u0.nbytes + p0.nbytes + A0.nbytes) / e2e_steps
-    d2h = out.nbytes / e2e_steps
-
-    forms = {}
-    if (not args.no_forms and rank == 0 and args.lattice == "d3q19" and not args.n
-            and launches == 1):
-        K = max(5, min(args.steps, 20))
-        for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("bf16_dev", F.FVLB_BF16_DEV),
-                           ("fp64", F.FVLB_FP64)):
-            forms[f"d3q19_256^3_{name}"] = form_rate(F, pr, prec, K, 2, stream)
-            torch.cuda.empty_cache()
-        pr2 = W.four_roll(n=2048, Wi=0.5, beta=0.5)
-        for name, prec in (("fp32", F.FVLB_FP32), ("fp16_dev", F.FVLB_FP16_DEV)):
-            forms[f"d2q9_2048^2_four_roll_{name}"] = form_rate(F, pr2, prec, K, 2, stream)
-        # The comparison of Tables 1-2: the present scheme against the original
-        # one (stress divergence by finite differences as a body force).  Each
-        # in the fused form (present: one launch; original: stress, its
-        # divergence and the fused step, three launches) and the split form
-        # (present: two launches; original: stress, velocity, collision).
-        for key, p in (("d3q19_256^3_fp32", pr), ("d2q9_2048^2_four_roll_fp32", pr2)):
-            split = form_rate(F, p, F.FVLB_FP32, K, 2, stream, kernel=1)
-            orig_split = form_rate(F, p, F.FVLB_FP32, K, 2, stream, kernel=1,
-                                   scheme=F.FVLB_SCHEME_ORIGINAL)
-            orig = form_rate(F, p, F.FVLB_FP32, K, 2, stream, kernel=0,
-                             scheme=F.FVLB_SCHEME_ORIGINAL)
-            fused_ms = (forms[key]["ms_per_step"] if key in forms        # D2Q9
-                        else 1e3 * dt / args.steps if args.precision == "fp32"  # headline
-                        else None)
-            orig_split["time_ratio_present_split_over_original_split"] = round(
-                split["ms_per_step"] / orig_split["ms_per_step"], 3)
-            if fused_ms is not None:
-                orig["time_ratio_present_fused_over_original_fused"] = round(
-                    fused_ms / orig["ms_per_step"], 3)
-            forms[f"{key}_split"] = split
-            forms[f"{key}_original"] = orig
-            forms[f"{key}_original_split"] = orig_split
-            torch.cuda.empty_cache()
-        for name, prec in (("fp16_dev", F.FVLB_FP16_DEV), ("fp32", F.FVLB_FP32)):
-            forms[f"batched_512_d2q9_{name}"] = batch_rate(F, prec, stream)
-            torch.cuda.empty_cache()
-        obo = one_by_one_rate(F, F.FVLB_FP32, stream)
-        obo["batched_fp32_speedup"] = round(forms["batched_512_d2q9_fp32"]["mlups"] / obo["mlups"], 2)
-        forms["d2q9_512_instances_fp32_one_by_one"] = obo
-        torch.cuda.empty_cache()
-        # other constitutive models (relaxation part of chi): same bytes per update
-        for name, model, par in (("giesekus", F.FVLB_MODEL_GIESEKUS, 0.3),
-                                 ("ptt_exp", F.FVLB_MODEL_PTT_EXP, 0.25)):
-            pm = tgv_problem(WORKLOAD["n"])
-            pm.model, pm.mpar = model, par
-            forms[f"d3q19_256^3_fp32_{name}"] = form_rate(F, pm, F.FVLB_FP32, K, 2, stream)
-            torch.cuda.empty_cache()
-        forms["d3q19_256^3_fp32_learned_closure"] = closure_rate(F, stream)
-        torch.cuda.empty_cache()
-        for k, v in forms.items():
-            v["frac_of_hbm_peak"] = round(v["gbs_algorithmic"] / peak, 3)
-        torch.cuda.synchronize()
-
-    if rank != 0:
-        return
-    cpu = None
-    if world == 1 and not args.no_cpu:
-        rate, steps, n = oracle_rate()
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 CPU oracle, single thread, D3Q19 Taylor-Green 32^3 "
-                         f"({n} sites, same Re/Wi/beta), {steps} steps in ~12 s"}
-    line = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.precision, "f32 (16-bit storage)"),
-        "data": "synthetic (seeded Taylor-Green initial field of Sec. 3.4)",
-        "config": config_dict(args, "" if launches == 1 else "original scheme"),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                     "algorithmic_bytes_per_launch": bpu * sites,
-                     "bytes_per_update": bpu, "peak_source": f"{which} hbm_gbs (copy)",
-                     "kernel": kernel_label(args.lattice, args.precision)
-                               + ("" if launches == 1 else
-                                  "; original scheme: k_taup + k_fdiv + this kernel "
-                                  "(ORIG) per step, state bytes over the step time")},
-        "e2e": {"value": round(sites * e2e_steps / e2e_dt / 1e6, 1), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "note": "fvlb_init_fields from pinned host memory + K steps + "
-                        "fvlb_fields(U) to pinned host memory"},
-        "gpu_launches": args.steps * launches,
-        "clocks": clk.summary(),
-        "diagnostics": {"KE": diag["KE"], "PE": diag["PE"], "nonfinite": diag["nonfinite"]},
-        "forms": forms,
-        "cpu_baseline": cpu,
-    }
-    print(json.dumps(line), flush=True)
+def run_forms(args):
+    """Every form, each in a subprocess of its own; prints one JSON line per
+    form (a failed form prints its exit status instead)."""
+    for name in list(FORMS) + SPECIAL_FORMS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--form", name,
+               "--steps", str(args.steps)]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode == 0 and lines:
+                print(lines[-1], flush=True)
+            else:
+                print(json.dumps({"form": name, "failed": r.returncode,
+                                  "stderr_tail": r.stderr[-600:]}), flush=True)
+        except subprocess.TimeoutExpired:
+            print(json.dumps({"form": name, "failed": "timeout"}), flush=True)
 
 
 def main():
@@ -567,16 +676,17 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="(accepted; forms run only with --forms)")
+    ap.add_argument("--forms", action="store_true", help="time every other form, one process each")
     ap.add_argument("--lattice", default="d3q19", choices=["d3q19", "d2q9"])
     ap.add_argument("--n", type=int, default=0, help="grid nodes per axis (0: the default workload)")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp64", "fp32", "fp16_dev", "bf16_dev", "fp16_dev_sr", "bf16_dev_sr"])
     ap.add_argument("--scheme", default="present", choices=["present", "original"],
                     help="original: the comparison scheme of Tables 1-2 (profiling)")
-    ap.add_argument("--form", default="", choices=["", "batched_fp32", "batched_fp16", "closure"],
-                    help="time only this form and print its line (profiling)")
+    ap.add_argument("--form", default="", choices=[""] + list(FORMS) + SPECIAL_FORMS,
+                    help="time only this form and print its line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -585,6 +695,9 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.forms:
+        run_forms(args)
         return
     if args.form:
         run_form(args)

@@ -173,34 +173,62 @@ def womersley(L: int = 64, nx: int = 4, gamma: float = 3.070, beta: float = 0.5,
 
 def taylor_green_3d(n: int = 128, U0: float = 0.02, Re: float = 100.0,
                     Wi: float = 1.0, beta: float = 0.5, theta: float = math.pi / 2,
-                    length: str = "2pi") -> Problem:
+                    length: str = "2pi", fields: bool = True, out_u=None,
+                    out_p=None) -> Problem:
     """Periodic n^3 box, initial velocity and pressure of Sec. 3.4 (theta =
     pi/2), zero initial polymer stress.  The characteristic length is
     L = n / (2 pi) (the box spans 2 pi) or L = n; nu = U0 L / Re, lambda =
-    Wi L / U0, nu_s = beta nu."""
+    Wi L / U0, nu_s = beta nu.
+
+    The fields are formed one z-plane at a time from per-axis sine and cosine
+    tables, so building them holds nothing beyond the outputs (u: n^3 x 3,
+    p: n^3 doubles).  ``out_u`` / ``out_p`` (C-contiguous float64 arrays of
+    those shapes, e.g. page-locked host buffers) receive them in place;
+    ``fields=False`` leaves u0 and p0 unset."""
     L = n / (2.0 * math.pi) if length == "2pi" else float(n)
     nu = U0 * L / Re
     nu_s = beta * nu
     nu_p = nu - nu_s
     tau_s = tau_from_nu(nu_s)
     lam = Wi * L / U0
-    k = 2.0 * math.pi / n
-    z, y, x = _coords((n, n, n))
-    X, Y, Z = k * x, k * y, k * z
-    a = 2.0 * U0 / math.sqrt(3.0)
-    u = np.stack([
-        a * math.sin(theta + 2.0 * math.pi / 3.0) * np.sin(X) * np.cos(Y) * np.cos(Z),
-        a * math.sin(theta - 2.0 * math.pi / 3.0) * np.cos(X) * np.sin(Y) * np.cos(Z),
-        a * math.sin(theta) * np.cos(X) * np.cos(Y) * np.sin(Z)], axis=-1)
-    p = U0 ** 2 * ((np.cos(2 * X) * np.cos(2 * Y) + 2 * np.cos(2 * Z)) / 12.0
-                   + (np.cos(2 * X) * np.cos(2 * Z) + 2 * np.cos(2 * Y)) / 48.0
-                   + (np.cos(2 * Y) * np.cos(2 * Z) + 2 * np.cos(2 * X)) / 48.0)
     pr = Problem("taylor_green_3d", D3Q19, n, n, n, tau_s, nu_p, lam,
                  FORCE_NONE, (0.0, 0.0, 0.0), 0.0, 0.0, 0)
-    pr.u0 = u
-    pr.p0 = p
     pr.meta = dict(U0=U0, Re=Re, Wi=Wi, beta=beta, nu_s=nu_s, nu_p=nu_p, L=L)
+    if fields:
+        pr.u0, pr.p0 = taylor_green_3d_fields(n, U0, theta, out_u, out_p)
     return pr
+
+
+def taylor_green_3d_fields(n: int, U0: float = 0.02, theta: float = math.pi / 2,
+                           out_u=None, out_p=None):
+    """Initial velocity and pressure of the Sec. 3.4 vortex on the n^3 nodes
+    (x = k i, k = 2 pi / n): u = (2 U0 / sqrt 3) [sin(theta + 2 pi/3) sin x cos y cos z,
+    sin(theta - 2 pi/3) cos x sin y cos z, sin(theta) cos x cos y sin z] and the
+    pressure that balances it.  Returns (u [n, n, n, 3], p [n, n, n])."""
+    k = 2.0 * math.pi / n
+    t = k * np.arange(n, dtype=np.float64)
+    s1, c1 = np.sin(t), np.cos(t)
+    c2 = np.cos(2 * t)
+    a = 2.0 * U0 / math.sqrt(3.0)
+    ax = a * math.sin(theta + 2.0 * math.pi / 3.0)
+    ay = a * math.sin(theta - 2.0 * math.pi / 3.0)
+    az = a * math.sin(theta)
+    u = np.empty((n, n, n, 3)) if out_u is None else out_u
+    p = np.empty((n, n, n)) if out_p is None else out_p
+    if u.shape != (n, n, n, 3) or p.shape != (n, n, n):
+        raise ValueError("out_u / out_p have the wrong shape")
+    X, Y = s1[None, :], s1[:, None]          # sin over x (last axis) and y
+    CX, CY = c1[None, :], c1[:, None]
+    C2X, C2Y = c2[None, :], c2[:, None]
+    for iz in range(n):
+        sz, cz, c2z = s1[iz], c1[iz], c2[iz]
+        u[iz, :, :, 0] = ax * X * CY * cz
+        u[iz, :, :, 1] = ay * CX * Y * cz
+        u[iz, :, :, 2] = az * CX * CY * sz
+        p[iz] = U0 ** 2 * ((C2X * C2Y + 2 * c2z) / 12.0
+                           + (C2X * c2z + 2 * C2Y) / 48.0
+                           + (C2Y * c2z + 2 * C2X) / 48.0)
+    return u, p
 
 
 def taylor_green_2d(n: int = 64, U0: float = 0.01, tau_s: float = 0.8,
