@@ -31,7 +31,7 @@
  *   R4  The stress distributions h use the same lattice as the flow.
  *   R5  Walls are halfway bounce-back for both f and h.
  *   R6  The body force is evaluated at the time level of the step, t_n = n.
- *   R7  Initial state: f = f^eq(p0, u0), h = h^eq(A0, u0).
+ *   R7  Initial state: f = f^eq(p0, u0), h = h^eq(A0, u0) (with R10).
  *   R8  The "original" scheme the paper compares against (Sec. 1, Tables 1
  *       and 2) adds the polymer stress divergence to the momentum equation
  *       as a body force instead of the fluctuation term: f^B = 0 and
@@ -53,6 +53,15 @@
  *       (PTT without the slip parameter), tau_p = (eta_p/lambda) M in all
  *       four.  The trace runs over the D x D tensor; in 2D A_zz = 1, so M has
  *       no z entries and the 2D restriction is exact.
+ *   R10 The stress equilibrium has zeroth moment A (Sec. 2.3: A is the
+ *       zeroth moment of h, and the collision conserves it apart from the
+ *       source).  The weights typed in below sum to 1 - 5.6e-17 in FP64,
+ *       and with h ~ w_i A every collision would then scale A by about
+ *       1 - 1.1e-16 (1/tau_h ~ 2); over thousands of steps that drift is
+ *       a relative error of 1e-12 in A - I where |A - I| << |A|.  So the
+ *       rest direction's equilibrium is the zeroth-moment condition solved
+ *       for it, h^eq_0 = A - sum_{i>=1} h^eq_i, which equals w_0 A exactly
+ *       for exact weights.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -394,10 +403,13 @@ void orc_init(orc *o, const double *u0, const double *p0, const double *A0) {
     for (int ab = 0; ab < o->DD; ++ab) {
       const int a = ab / o->D, b = ab % o->D;
       const double Aab = A0 ? A0[s * o->DD + ab] : (a == b ? 1.0 : 0.0);
-      for (int i = 0; i < o->Q; ++i) {
-        o->h[(s * o->DD + ab) * o->Q + i] =
-            L->w[i] * Aab * (1.0 + dot3(L->c[i], u) / CS2);
+      double *h = &o->h[(s * o->DD + ab) * o->Q];
+      double moving = 0.0;   /* rest direction from the zeroth moment (R10) */
+      for (int i = 1; i < o->Q; ++i) {
+        h[i] = L->w[i] * Aab * (1.0 + dot3(L->c[i], u) / CS2);
+        moving += h[i];
       }
+      h[0] = Aab - moving;
     }
     for (int ab = 0; ab < o->DD; ++ab) o->chi_old[s * o->DD + ab] = 0.0;
   }
@@ -616,15 +628,23 @@ static void step_once(orc *o) {
           o->f_new[d * Q + j] = post;
         }
 
-        /* h: collide and stream */
+        /* h: collide and stream.  h^eq_i = w_i A (1 + c_i.u / c_s^2) for
+         * i >= 1; the rest direction takes what the zeroth moment leaves,
+         * h^eq_0 = A - sum_{i>=1} h^eq_i (reading R10). */
         for (int ab = 0; ab < DD; ++ab) {
           const double *h = &o->h[(s * DD + ab) * Q];
+          double heq[19];
+          double moving = 0.0;
+          for (int i = 1; i < Q; ++i) {
+            heq[i] = L->w[i] * A[ab] * (1.0 + dot3(L->c[i], u) / CS2);
+            moving += heq[i];
+          }
+          heq[0] = A[ab] - moving;
           for (int i = 0; i < Q; ++i) {
             const double cu = dot3(L->c[i], u);
-            const double heq = L->w[i] * A[ab] * (1.0 + cu / CS2);
             const double phi =
                 L->w[i] * (1.0 + (1.0 - 0.5 / o->tau_h) * cu / CS2);
-            const double post = h[i] - (h[i] - heq) / o->tau_h + phi * chi[ab] +
+            const double post = h[i] - (h[i] - heq[i]) / o->tau_h + phi * chi[ab] +
                                 0.5 * phi * (chi[ab] - chi_old[ab]);
             int j;
             const long d = stream_dest(o, p, i, &j);

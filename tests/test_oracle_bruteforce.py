@@ -268,3 +268,63 @@ def test_bruteforce_models(lat, model, par):
     pr.model, pr.mpar = model, par
     pr.u0, pr.p0, pr.A0 = W.random_smooth(lat, pr.shape, seed=21, U=0.03, dA=0.6)
     _compare(pr, 15)
+
+
+# ---------------------------------------------------------------------------
+# Extended precision: the same tensor forms in long double with weights that
+# sum to 1 (exact fractions), against the FP64 oracle on a slow, strongly
+# stressed channel, where A - I is a small part of A.  With the FP64 weights
+# (which sum to 1 - 5.6e-17) in an equilibrium w_i A, every collision would
+# scale A by about 1 - 1.1e-16 (1/tau_h ~ 2), a drift of 2e-13 (64 nodes,
+# 1000 steps) and 5e-12 (128 nodes, 300 steps) in A - I; the oracle's rest
+# equilibrium taken from the zeroth-moment condition (its reading R10)
+# removes it.
+# ---------------------------------------------------------------------------
+
+class NumpyLBLong(NumpyLB):
+    """NumpyLB in long double: exact-fraction weights, the least-norm f^B
+    operator refined in long double (Newton-Schulz iteration on the FP64
+    pseudo-inverse), force tables in long double."""
+
+    def __init__(self, pr):
+        super().__init__(pr)
+        LD = np.longdouble
+        self.c = self.c.astype(LD)
+        if self.Q == 9:
+            w = [LD(4) / 9] + [LD(1) / 9] * 4 + [LD(1) / 36] * 4
+        else:
+            w = [LD(1) / 3] + [LD(1) / 18] * 6 + [LD(1) / 36] * 12
+        self.w = np.array(w, dtype=LD)
+        Cm = self.Cmat.astype(LD)
+        P = self.P.astype(LD)
+        for _ in range(3):
+            P = 2 * P - P @ Cm @ P
+        self.P = P
+
+    def init(self, u, p, A):
+        super().init(u, p, A)
+        LD = np.longdouble
+        self.f = self.f.astype(LD)
+        self.h = self.h.astype(LD)
+        self.chi_old = self.chi_old.astype(LD)
+
+    def force(self, t):
+        return super().force(t).astype(np.longdouble)
+
+
+@pytest.mark.parametrize("L,steps,bound", [(64, 1000, 1e-13), (128, 300, 2e-12)])
+def test_oracle_against_extended_precision(L, steps, bound):
+    pr = W.poiseuille(L=L, nx=4, Wi=1.0, beta=0.1)
+    nb = NumpyLBLong(pr)
+    nb.init(pr.u0, pr.p0, pr.A0)
+    for _ in range(steps):
+        nb.step()
+    o = O.Oracle(pr.lattice, **pr.oracle_kwargs())
+    o.init(u=pr.u0, p=pr.p0, A=pr.A0)
+    o.step(steps)
+    u, A = nb.fields()
+    I = np.eye(2)
+    T = np.asarray(A - I, dtype=np.float64)
+    err = np.linalg.norm((o.A() - I) - T) / np.linalg.norm(T)
+    assert err < bound, err
+    assert np.linalg.norm(o.u() - np.asarray(u, np.float64)) / np.linalg.norm(np.asarray(u, np.float64)) < 1e-13
