@@ -104,6 +104,8 @@ def lib():
             L.orc_pressure.restype = ctypes.c_double
             L.orc_force_at.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_long, dp]
+            L.orc_repair.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.orc_repair.restype = ctypes.c_long
             _lib = L
     return _lib
 
@@ -295,6 +297,12 @@ class Oracle:
         D, N, Q = self.D, self.N, self.Q
         lib().orc_set_state(self._h, _dp(_f64(f, (N * Q,))), _dp(_f64(h, (N * D * D * Q,))),
                             _dp(_f64(chi, (N * D * D,))), int(bool(first)), int(t))
+
+    def repair(self, eps: float) -> int:
+        """High-Wi repair (reading R11 of fvlb_oracle.c): clip the
+        eigenvalues of A below eps at every node; returns the number of
+        nodes changed."""
+        return int(lib().orc_repair(self._h, float(eps)))
 
     def force_at(self, x, y, z=0, t=None):
         out = np.zeros(3)

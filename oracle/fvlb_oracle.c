@@ -53,6 +53,14 @@
  *       (PTT without the slip parameter), tau_p = (eta_p/lambda) M in all
  *       four.  The trace runs over the D x D tensor; in 2D A_zz = 1, so M has
  *       no z entries and the 2D restriction is exact.
+ *   R11 High-Wi repair (the paper runs the four-roll mill up to Wi = 5,
+ *       Sec. 3.1, and leaves robustness at high Wi to future work, Sec. 4):
+ *       A must stay symmetric positive definite; a node whose A = sum_i h_i
+ *       has its smallest eigenvalue below a floor eps is given
+ *       A' = V max(Lambda, eps) V^T (eigenvalues clipped, eigenvectors
+ *       kept) by adding w_i (A' - A) to its stress populations, which
+ *       changes the zeroth moment of h only (sum_i w_i c_i = 0).  Applied
+ *       between steps, on request.
  *   R10 The stress equilibrium has zeroth moment A (Sec. 2.3: A is the
  *       zeroth moment of h, and the collision conserves it apart from the
  *       source).  The weights typed in below sum to 1 - 5.6e-17 in FP64,
@@ -706,6 +714,92 @@ int orc_fields(orc *o, int which, double *out) {
         }
       }
   return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * High-Wi repair of the conformation (reading R11).  Eigen-decomposition of
+ * a symmetric D x D matrix by cyclic Jacobi rotations (each rotation zeroes
+ * one off-diagonal entry; sweeps until the off-diagonal part is below 1e-300
+ * or 50 sweeps), then A' = V max(Lambda, eps) V^T.
+ * ------------------------------------------------------------------------- */
+static void sym_eig(int D, const double *A, double *lam, double *V) {
+  double a[3][3], v[3][3];
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      a[r][c] = A[T(D, r, c)];
+      v[r][c] = r == c ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int r = 0; r < D; ++r)
+      for (int c = r + 1; c < D; ++c) off += a[r][c] * a[r][c];
+    if (off < 1e-300) break;
+    for (int p = 0; p < D; ++p)
+      for (int q = p + 1; q < D; ++q) {
+        if (a[p][q] == 0.0) continue;
+        /* rotation angle: tan(2 theta) = 2 a_pq / (a_qq - a_pp) */
+        const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < D; ++k) {   /* A <- A J (columns p, q) */
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = cs * akp - sn * akq;
+          a[k][q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < D; ++k) {   /* A <- J^T A (rows p, q) */
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = cs * apk - sn * aqk;
+          a[q][k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < D; ++k) {   /* V <- V J */
+          const double vkp = v[k][p], vkq = v[k][q];
+          v[k][p] = cs * vkp - sn * vkq;
+          v[k][q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  for (int k = 0; k < D; ++k) {
+    lam[k] = a[k][k];
+    for (int r = 0; r < D; ++r) V[T(D, r, k)] = v[r][k];   /* column k */
+  }
+}
+
+/* Every node whose A = sum_i h_i has its smallest eigenvalue below eps (or a
+ * non-finite entry: left as it is and counted) gets A' = V max(Lambda, eps)
+ * V^T, by adding w_i (A' - A) to each of its stress populations; returns
+ * the number of nodes changed. */
+long orc_repair(orc *o, double eps) {
+  const lattice_t *L = &o->L;
+  const int Q = o->Q, D = o->D, DD = o->DD;
+  long count = 0;
+  for (long s = 0; s < o->N; ++s) {
+    double A[9], lam[3], V[9];
+    int finite = 1;
+    for (int ab = 0; ab < DD; ++ab) {
+      double acc = 0.0;
+      for (int i = 0; i < Q; ++i) acc += o->h[(s * DD + ab) * Q + i];
+      A[ab] = acc;
+      finite &= isfinite(acc);
+    }
+    if (!finite) {
+      ++count;
+      continue;
+    }
+    sym_eig(D, A, lam, V);
+    double lmin = lam[0];
+    for (int k = 1; k < D; ++k) lmin = lam[k] < lmin ? lam[k] : lmin;
+    if (lmin >= eps) continue;
+    ++count;
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) {
+        double An = 0.0;
+        for (int k = 0; k < D; ++k)
+          An += V[T(D, a, k)] * (lam[k] > eps ? lam[k] : eps) * V[T(D, b, k)];
+        const double dA = An - A[T(D, a, b)];
+        for (int i = 0; i < Q; ++i) o->h[(s * DD + T(D, a, b)) * Q + i] += L->w[i] * dA;
+      }
+  }
+  return count;
 }
 
 /* Raw state access: f [N][Q], h [N][DD][Q], chi_old [N][DD]. */
