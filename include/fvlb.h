@@ -82,7 +82,19 @@ typedef struct {
  * FP32 and keep chi in FP32; FP16_DEV and BF16_DEV round to nearest when
  * storing, FP16_DEV_SR and BF16_DEV_SR round stochastically (unbiased, with
  * random bits from a counter-based hash of site and step, so runs are
- * reproducible). */
+ * reproducible).  So that rounding to 16 bits every step does not bias
+ * slowly evolving flows, the 16-bit forms store
+ *   f as KF (f_i - e_i(U)), the deviation from the velocity part of the
+ *     equilibrium, e_i(U) = w_i (3 c_i.U + 4.5 (c_i.U)^2 - 1.5 U.U), at the
+ *     velocity U of the receiving node in the step that wrote it, scaled
+ *     by KF = 4096 (FP16) or 1 (BF16); U itself in FP32, U[D][pitch]
+ *     right after f[Q][pitch] in the same buffer;
+ *   the rest stress population h'_ab,0 in FP32, h0[C][pitch] right after
+ *     h'[C][Q][pitch] (whose i = 0 slots are unused), where each store
+ *     also adds the rounding residuals of the component's 16-bit
+ *     populations, so that their sum carries no rounding bias.
+ * Bytes per node update: 196 (D2Q9) and 628 (D3Q19), against 312 and 1112
+ * for FP32. */
 enum {
   FVLB_FP64 = 0,
   FVLB_FP32 = 1,
@@ -260,6 +272,21 @@ int fvlb_reduce(fvlb_t h, double out[8]);
  * (at rest) if needed. */
 int fvlb_conformation(fvlb_t h, double out[3]);
 
+/* High-Wi repair of the conformation.  The paper runs the four-roll mill up
+ * to Wi = 5 (Sec. 3.1) and leaves robustness at high Wi to future work
+ * (Sec. 4); what fails there first is the positive definiteness of A.  For
+ * every node whose A has its smallest eigenvalue below eps (> 0), A is
+ * replaced by V max(Lambda, eps) V^T (eigenvalues clipped, eigenvectors
+ * kept: cyclic Jacobi rotations in FP64), applied as h'_{ab,i} +=
+ * w_i (A' - A)_ab on the node's stress populations, which leaves every
+ * other moment of h unchanged.  Nodes with a non-finite A are counted and
+ * left as they are.  *repaired (may be NULL) receives the number of nodes
+ * changed.  Acts on the current state between steps; call it every few
+ * steps (with fvlb_conformation to see when it is needed).  16-bit forms:
+ * the changed populations are rounded again, their residual kept in the
+ * FP32 rest population.  Errors: FVLB_EINVAL for eps <= 0 or not finite. */
+int fvlb_repair_conformation(fvlb_t h, double eps, long long *repaired);
+
 /* The diagnostics of fvlb_reduce for a state the caller holds in its own
  * device memory, with no device allocation at all.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
@@ -270,24 +297,32 @@ int fvlb_conformation(fvlb_t h, double out[3]);
  *   lattice, storage  FVLB_D2Q9 / FVLB_D3Q19 and an FVLB_FP64 ... storage
  *   nx, ny, nz        grid (nz ignored in 2D); N = nx ny nz
  *   f                 device array f[Q][pitch] of the storage type
+ *                     (16-bit forms: followed by U[D][pitch] in FP32)
  *   h                 device array h'[C][Q][pitch], h' = h - w_i delta_ab
- *                     (the layout of fvlb_save_state's image after its
- *                     64-byte header)
+ *                     (16-bit forms: followed by h0[C][pitch] in FP32);
+ *                     the layouts of fvlb_save_state's image after its
+ *                     64-byte header
  *   pitch             elements between population arrays, >= N
  *   eta_p, lambda     polymer viscosity and relaxation time (PE = tr tau_p/2)
  *   F                 host array of the uniform body force entering
  *                     u = sum c_i f_i + F/2, or NULL for 0
- *   out               device array of 8 doubles, filled as by fvlb_reduce
- *                     (no FVLB_EUNSTABLE check: read out[6])
+ *   out               device array of 8 doubles, filled as fvlb_reduce
+ *                     fills it for a state of the present scheme with a
+ *                     uniform body force (no FVLB_EUNSTABLE check: read
+ *                     out[6]); for a four-roll force or an original-scheme
+ *                     state, whose force varies from node to node, u and
+ *                     KE are those of the uniform force F given here
  *   stream            cudaStream_t, or NULL for the legacy default stream
  * The work is enqueued on `stream` and the call returns without waiting.
  * Scratch: the per-block partial sums live in a file-scope device array of
  * 1024 x 8 doubles (64 KiB) that every GPU using the library keeps until
- * the process exits; N beyond the library's limit is rejected with
- * FVLB_EINVAL.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the array: calls whose kernels overlap on the
- * GPU race and give wrong results. */
+ * the process exits; a grid beyond the library's limit (Q * pitch >= 2^32)
+ * is rejected with FVLB_EINVAL (the number of partial sums is capped at
+ * 1024 for any N).  The first call on a device, and the first after its
+ * context was reset, looks up the array's device address
+ * (cudaGetSymbolAddress), so make that call before any stream capture.  All
+ * calls share the array: calls whose kernels overlap on the GPU race and
+ * give wrong results.  Rejected calls leave `out` untouched. */
 int fvlb_reduce_noalloc(int lattice, int storage, int nx, int ny, int nz,
                         const void *f, const void *h, long long pitch,
                         double eta_p, double lambda, const double F[3],

@@ -195,9 +195,10 @@ int allocate(fvlb_t h) {
   const size_t sb = storage_bytes(h->storage), xb = chi_bytes(h->storage);
   const size_t P = (size_t)h->pitch;
   const size_t rb = h->storage == FVLB_FP64 ? 8 : 4;
+  (void)sb;
   for (int b = 0; b < 2; ++b) {
-    h->f[b] = dev_alloc(h, sb * h->Q * P);
-    h->h[b] = dev_alloc(h, sb * (size_t)h->C * h->Q * P);
+    h->f[b] = dev_alloc(h, fvlb::f_buffer_bytes(h->storage, h->Q, h->D, P));
+    h->h[b] = dev_alloc(h, fvlb::h_buffer_bytes(h->storage, h->C, h->Q, P));
   }
   h->chi = dev_alloc(h, xb * h->C * P);
   h->ubuf = dev_alloc(h, rb * h->D * P);
@@ -208,6 +209,12 @@ int allocate(fvlb_t h) {
   bool ok = h->f[0] && h->f[1] && h->h[0] && h->h[1] && h->chi && h->ubuf && h->part && h->red &&
             h->cl_count;
   if (ok && cudaMemset(h->cl_count, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) ok = false;
+  // 16-bit forms: the i = 0 slots of the 16-bit stress arrays are never
+  // used (the rest populations are FP32); zero them once so that checkpoint
+  // images hold no leftover bytes
+  if (ok && fvlb::v2_storage(h->storage))
+    for (int b = 0; b < 2 && ok; ++b)
+      ok = cudaMemset(h->h[b], 0, fvlb::h_buffer_bytes(h->storage, h->C, h->Q, P)) == cudaSuccess;
   if (ok && h->force.kind == FVLB_FORCE_FOUR_ROLL) {
     const int n = 2 * (h->nx + h->ny);
     h->tables = dev_alloc(h, rb * n);
@@ -306,8 +313,8 @@ int comps(fvlb_t h, int which) {
 
 size_t state_bytes(fvlb_t h) {
   const size_t P = (size_t)h->pitch;
-  return sizeof(StateHeader) + storage_bytes(h->storage) * (size_t)h->Q * P * (1 + h->C) +
-         chi_bytes(h->storage) * (size_t)h->C * P;
+  return sizeof(StateHeader) + fvlb::f_buffer_bytes(h->storage, h->Q, h->D, P) +
+         fvlb::h_buffer_bytes(h->storage, h->C, h->Q, P) + chi_bytes(h->storage) * (size_t)h->C * P;
 }
 
 }  // namespace
@@ -667,6 +674,26 @@ int fvlb_conformation(fvlb_t h, double out[3]) {
   return FVLB_OK;
 }
 
+int fvlb_repair_conformation(fvlb_t h, double eps, long long* repaired) {
+  if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
+  Range range("fvlb_repair_conformation");
+  if (!(eps > 0.0) || !std::isfinite(eps))
+    return fail(h, FVLB_EINVAL, "fvlb_repair_conformation: eps must be finite and > 0");
+  int r = ensure_state(h, true);
+  if (r != FVLB_OK) return r;
+  StepDesc d = make_desc(h);
+  // the count reuses the handle's reduction output (8 doubles)
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(h->red);
+  cudaError_t e = h->lattice == FVLB_D2Q9 ? fvlb::repair_d2q9(d, eps, cnt)
+                                          : fvlb::repair_d3q19(d, eps, cnt);
+  unsigned long long host = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, cnt, sizeof(host), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_repair_conformation");
+  if (repaired) *repaired = (long long)host;
+  return FVLB_OK;
+}
+
 int fvlb_set_closure(fvlb_t h, fvlb_mlp_t m, double tol) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   if (m && fvlb::mlp_lattice(m) != h->lattice)
@@ -734,8 +761,10 @@ int fvlb_save_state(fvlb_t h, void* host_buf, size_t bytes) {
   char* p = static_cast<char*>(host_buf);
   std::memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
-  const size_t P = (size_t)h->pitch, sb = storage_bytes(h->storage);
-  const size_t bf = sb * h->Q * P, bh = sb * (size_t)h->C * h->Q * P, bc = chi_bytes(h->storage) * h->C * P;
+  const size_t P = (size_t)h->pitch;
+  const size_t bf = fvlb::f_buffer_bytes(h->storage, h->Q, h->D, P),
+               bh = fvlb::h_buffer_bytes(h->storage, h->C, h->Q, P),
+               bc = chi_bytes(h->storage) * h->C * P;
   cudaError_t e = cudaMemcpyAsync(p, h->f[h->cur], bf, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + bf, h->h[h->cur], bh, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + bf + bh, h->chi, bc, cudaMemcpyDeviceToHost, h->stream);
@@ -758,8 +787,10 @@ int fvlb_load_state(fvlb_t h, const void* host_buf, size_t bytes) {
   if (r != FVLB_OK) return r;
   h->bad_t = -1;
   const char* p = static_cast<const char*>(host_buf) + sizeof(hd);
-  const size_t P = (size_t)h->pitch, sb = storage_bytes(h->storage);
-  const size_t bf = sb * h->Q * P, bh = sb * (size_t)h->C * h->Q * P, bc = chi_bytes(h->storage) * h->C * P;
+  const size_t P = (size_t)h->pitch;
+  const size_t bf = fvlb::f_buffer_bytes(h->storage, h->Q, h->D, P),
+               bh = fvlb::h_buffer_bytes(h->storage, h->C, h->Q, P),
+               bc = chi_bytes(h->storage) * h->C * P;
   cudaError_t e = cudaMemcpyAsync(h->f[h->cur], p, bf, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->h[h->cur], p + bf, bh, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->chi, p + bf + bh, bc, cudaMemcpyHostToDevice, h->stream);
@@ -772,8 +803,7 @@ int fvlb_load_state(fvlb_t h, const void* host_buf, size_t bytes) {
 
 int fvlb_bytes_per_update(fvlb_t h, double* bytes) {
   if (!h || !bytes) return fail(h, FVLB_EINVAL, "fvlb_bytes_per_update: NULL argument");
-  *bytes = 2.0 * (h->Q + (double)h->C * h->Q) * storage_bytes(h->storage) +
-           2.0 * h->C * chi_bytes(h->storage);
+  *bytes = fvlb::bytes_per_update(h->storage, h->Q, h->C, h->D);
   return FVLB_OK;
 }
 

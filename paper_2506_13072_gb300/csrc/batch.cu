@@ -365,8 +365,11 @@ int fvlb_batch_create(fvlb_batch_t* out, int lattice, int count, const fvlb_inst
     b->h_off.push_back(b->h_total);
     b->chi_off.push_back(b->chi_total);
     b->tab_off.push_back(b->tab_total);
-    b->f_total += kQ * P;
-    b->h_total += (long long)kC * kQ * P;
+    // (16-bit forms: each grid's buffers end with its FP32 arrays, U[D][P]
+    // and h0[C][P], counted here in 2-byte elements)
+    const long long ext = fvlb::v2_storage(storage) ? 2 : 0;
+    b->f_total += kQ * P + ext * kD * P;
+    b->h_total += (long long)kC * kQ * P + ext * kC * P;
     b->chi_total += kC * P;
     if (specs[i].force.kind == FVLB_FORCE_FOUR_ROLL) b->tab_total += 2 * (specs[i].nx + specs[i].ny);
     b->Nmax = std::max(b->Nmax, N);
@@ -547,7 +550,7 @@ int fvlb_batch_info(fvlb_batch_t b, long long* sites, double* bytes_per_update, 
   if (!b) return set_global_error(FVLB_EINVAL, "NULL batch");
   if (sites) *sites = b->sites;
   if (bytes_per_update)
-    *bytes_per_update = 2.0 * (kQ + (double)kC * kQ) * sbytes(b->storage) + 2.0 * kC * xbytes(b->storage);
+    *bytes_per_update = fvlb::bytes_per_update(b->storage, kQ, kC, kD);
   if (gx) *gx = b->gx;
   if (rows) *rows = b->mchunk;
   if (tuned_ms_per_step) *tuned_ms_per_step = b->tuned ? b->tuned_ms : 0.0;

@@ -9,6 +9,26 @@ namespace fvlb {
 
 enum Storage { kFP64 = 0, kFP32 = 1, kFP16Dev = 2, kBF16Dev = 3, kFP16DevSR = 4, kBF16DevSR = 5 };
 
+// Bytes of one population buffer of a grid.  The 16-bit forms append FP32
+// arrays to each buffer (fvlb_lattice.cuh): the velocity U[D][pitch] after
+// f[Q][pitch], the rest stress populations h0[C][pitch] after h[C][Q][pitch].
+inline bool v2_storage(int storage) { return storage >= kFP16Dev; }
+inline size_t elem_bytes(int storage) { return storage == kFP64 ? 8 : (storage == kFP32 ? 4 : 2); }
+inline size_t f_buffer_bytes(int storage, int Q, int D, size_t pitch) {
+  return elem_bytes(storage) * (size_t)Q * pitch + (v2_storage(storage) ? 4 * (size_t)D * pitch : 0);
+}
+inline size_t h_buffer_bytes(int storage, int C, int Q, size_t pitch) {
+  return elem_bytes(storage) * (size_t)C * Q * pitch + (v2_storage(storage) ? 4 * (size_t)C * pitch : 0);
+}
+// HBM bytes one node update reads and writes: populations, chi of the
+// previous step, and (16-bit forms) U and h0 in place of the 16-bit rest
+// stress populations
+inline double bytes_per_update(int storage, int Q, int C, int D) {
+  const double sb = (double)elem_bytes(storage), xb = storage == kFP64 ? 8.0 : 4.0;
+  if (!v2_storage(storage)) return 2.0 * (Q + (double)C * Q) * sb + 2.0 * C * xb;
+  return 2.0 * (Q * sb + 4.0 * D + C * (Q - 1) * sb + 4.0 * C) + 2.0 * C * xb;
+}
+
 // Precision-agnostic description of one launch; the launcher converts the
 // physics to the working precision of the storage type.
 struct StepDesc {
@@ -70,6 +90,9 @@ cudaError_t reduce_d3q19(const StepDesc& d, double* part, double* out);
 // conformation check: part as for the diagnostics, out[3] as fvlb_conformation
 cudaError_t conformation_d2q9(const StepDesc& d, double* part, double* out);
 cudaError_t conformation_d3q19(const StepDesc& d, double* part, double* out);
+// high-Wi repair: count (device) receives the number of nodes changed
+cudaError_t repair_d2q9(const StepDesc& d, double eps, unsigned long long* count);
+cudaError_t repair_d3q19(const StepDesc& d, double eps, unsigned long long* count);
 cudaError_t reduce_finalize(const double* part, int nparts, long long N, double* out,
                             cudaStream_t stream);
 // record the message returned by fvlb_last_error(NULL); returns code

@@ -59,21 +59,36 @@ __device__ __forceinline__ T* opaque(T* p) {
   return p;
 }
 
-// load f_i(s)
+// load f_i(s) (16-bit forms: s_i / KF + e_i(U) with the node's stored U)
 template <class L, class S>
 __device__ __forceinline__ void load_f(const S* __restrict__ f, long long pitch,
                                        long long s, RT<S> (&fv)[L::Q]) {
+  using R = RT<S>;
+  if constexpr (Store<S>::V2) {
+    const float* U = f_ext<L>(f, pitch);
+    R u[L::D];
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) fv[i] = Store<S>::ld(f + i * pitch + s);
+    for (int a = 0; a < L::D; ++a) u[a] = U[a * pitch + s];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      fv[i] = Store<S>::ld(f + i * pitch + s) * R(1.0f / Store<S>::KF) + feq_u<L, R>(i, u);
+  } else {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) fv[i] = Store<S>::ld(f + i * pitch + s);
+  }
 }
 
 // Stress populations are held as deviations from the rest equilibrium,
 // h'_{k,i} = h_{k,i} - w_i delta_k (delta_k = 1 on diagonal components), in
 // every storage precision: the conformation then enters as A - I = sum_i h'
 // without the cancellation of summing h ~ w_i A and subtracting I.
+// (16-bit forms: the rest population from its FP32 array)
 template <class L, class S>
 __device__ __forceinline__ RT<S> load_h(const S* __restrict__ h, long long pitch,
                                         long long s, int k, int i) {
+  if constexpr (Store<S>::V2) {
+    if (i == 0) return h_ext<L>(h, pitch)[k * pitch + s];
+  }
   return Store<S>::ld(h + (long long)(k * L::Q + i) * pitch + s);
 }
 
@@ -158,7 +173,8 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
                                              const Bufs<S>& b, long long s, int x,
                                              int y, int z, const RT<S> (&u)[L::D],
                                              const RT<S> (&gr)[L::D][L::D],
-                                             const RT<S> (&f)[L::Q], const RT<S> F[3]) {
+                                             const RT<S> (&f)[L::Q], const RT<S> F[3],
+                                             const RT<S>* __restrict__ ubuf = nullptr) {
   using R = RT<S>;
   using X = typename Store<S>::X;
   constexpr int D = L::D, Q = L::Q, C = L::C;
@@ -178,7 +194,8 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
     R a = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const R v = Store<S>::ld(hk + (long long)(k * Q + i) * P);
+      const R v = (Store<S>::V2 && i == 0) ? R(h_ext<L>(b.h_in, P)[k * P + s])
+                                           : Store<S>::ld(hk + (long long)(k * Q + i) * P);
       if (HOLD_H) hv[HOLD_H ? k : 0][HOLD_H ? i : 0] = v;
       a += v;
     }
@@ -218,6 +235,17 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
   // The destination of direction i is computed once and shared by f_i and
   // the C stress populations h_{k,i}.
   const S* hs = b.h_in + s;
+  // 16-bit forms: the rest stress populations (stored last, in FP32, with
+  // the rounding residuals of the component's other populations) and this
+  // node's velocity for the flow populations it receives next step
+  R h0post[Store<S>::V2 ? C : 1], hres[Store<S>::V2 ? C : 1];
+  if constexpr (Store<S>::V2) {
+#pragma unroll
+    for (int k = 0; k < C; ++k) hres[k] = R(0);
+    float* Uo = f_ext<L>(b.f_out, P);
+#pragma unroll
+    for (int a = 0; a < D; ++a) Uo[a * P + s] = float(u[a]);
+  }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (!HOLD_H && i % 3 == 0) hs = opaque(hs);
@@ -238,19 +266,44 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
     const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
     const R fBi = ORIG ? R(0) : fB_dir<L, R>(i, Ad, kB);
     const R fpost = f[i] - (f[i] - feq) * ph.inv_tau_f + fBi + Fi;
-    Store<S>::st(b.f_out + j * P + d, fpost, Store<S>::sr ? lcg_next(rng) : 0u);
+    if constexpr (Store<S>::V2) {
+      // deviation from e_j(u) of the receiving node (velocity of this step)
+      R ud[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) ud[a] = ubuf[a * P + d];
+      Store<S>::st(b.f_out + j * P + d, R(Store<S>::KF) * (fpost - feq_u<L, R>(j, ud)),
+                   Store<S>::sr ? lcg_next(rng) : 0u);
+    } else {
+      Store<S>::st(b.f_out + j * P + d, fpost, Store<S>::sr ? lcg_next(rng) : 0u);
+    }
 
     // stress: h* = h - (h - h^eq)/tau_h + phi_i src, phi_i = w_i [1 + (1 - 1/(2 tau_h)) c.u/c_s^2]
     const R phi = wi * (R(1) + ph.kh * R(3) * cu);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-      const R hi = HOLD_H ? hv[HOLD_H ? k : 0][HOLD_H ? i : 0]
-                          : reload_h<L, S>(hs, P, k, i);
+      R hi;
+      if (HOLD_H) hi = hv[HOLD_H ? k : 0][HOLD_H ? i : 0];
+      else if (Store<S>::V2 && i == 0) hi = R(h_ext<L>(b.h_in, P)[k * P + s]);
+      else hi = reload_h<L, S>(hs, P, k, i);
       // h^eq - w_i delta_k = w_i [(A - I)_k + A_k c_i.u / c_s^2]
       const R heq = wi * (Ad[k] + (Ad[k] + (diag<L>(k) ? R(1) : R(0))) * (R(3) * cu));
       const R post = hi - (hi - heq) * ph.inv_tau_h + phi * src[k];
-      store_h<L, S>(b.h_out, P, d, k, j, post, Store<S>::sr ? lcg_next(rng) : 0u);
+      if constexpr (Store<S>::V2) {
+        if (i == 0) {
+          h0post[k] = post;
+        } else {
+          S* q = b.h_out + (long long)(k * Q + j) * P + d;
+          hres[k] += post - Store<S>::st_r(q, post, Store<S>::sr ? lcg_next(rng) : 0u);
+        }
+      } else {
+        store_h<L, S>(b.h_out, P, d, k, j, post, Store<S>::sr ? lcg_next(rng) : 0u);
+      }
     }
+  }
+  if constexpr (Store<S>::V2) {
+    float* h0o = h_ext<L>(b.h_out, P);
+#pragma unroll
+    for (int k = 0; k < C; ++k) h0o[k * P + s] = float(h0post[k] + hres[k]);
   }
 }
 
@@ -394,7 +447,12 @@ struct TileCfg {
   static constexpr bool PF = (sizeof(S) == 4 || sizeof(S) == 2) && !CL;
   using CLS = typename std::conditional<CL, ClosureSmem<Sh::NG, C, NS>, NoClosureSmem>::type;
   static constexpr size_t kRing = sizeof(Vel<R, D>) * 4 * Sh::NE;
-  static constexpr size_t kStage1 = PF ? sizeof(S) * NPP * NCT + sizeof(X) * NCT : 0;
+  // 16-bit forms: the FP32 rest stress population of the thread's
+  // component and the node's stored velocity U, staged beside the rest
+  static constexpr bool V2 = Store<S>::V2;
+  static constexpr int NEX = V2 ? 1 + D : 1;
+  static constexpr size_t kStage1 =
+      PF ? sizeof(S) * NPP * NCT + sizeof(X) * NCT + (V2 ? sizeof(float) * NEX * NCT : 0) : 0;
   static constexpr size_t kEx1 = 2 * sizeof(R) * CP * NS;
   // dynamic shared memory: several rows per thread, or a staged 2D tile
   // (whose stage fills the static 48 KB and leaves no room for the
@@ -406,6 +464,7 @@ struct TileCfg {
   static constexpr int NBUF = (kRing + sizeof(CLS) + NST * kStage1 + 2 * kEx1 <= kLimit) ? 2 : 1;
   using Stage = typename std::conditional<PF, S[NST][NPP][NCT], int>::type;
   using StageX = typename std::conditional<PF, X[NST][NCT], int>::type;
+  using StageE = typename std::conditional<PF && V2, float[NST][NEX][NCT], int>::type;
   struct Smem {
     Vel<R, D> ring[4][Sh::NE];                    // velocity of planes m-1 .. m+2
     alignas(16) R sAd[NBUF][NS][CP];              // A - I of the tile nodes
@@ -413,6 +472,7 @@ struct TileCfg {
     CLS cls;                                      // learned closure (CL only)
     alignas(16) Stage stage;
     alignas(16) StageX stage_x;
+    alignas(16) StageE stage_e;
   };
   static constexpr size_t kDynamicBytes = kDynamic ? sizeof(Smem) : 0;
 };
@@ -455,6 +515,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   auto& cls = smp->cls;
   auto& stage = smp->stage;
   auto& stage_x = smp->stage_x;
+  auto& stage_e = smp->stage_e;
+  (void)stage_e;
   (void)cls;
   (void)stage;
   (void)stage_x;
@@ -498,8 +560,13 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     return true;
   };
   // velocity of ring slot e of plane q from its populations fv (loaded by
-  // the caller when `ok`), into the plane's ring slot
-  auto fill_store = [&](int e, bool ok, int mm, int gx, int gy, const R (&fv)[Q], int q) {
+  // the caller when `ok`), into the plane's ring slot.  16-bit forms: fv
+  // holds the Q stored values and then the node's stored velocity U, and
+  // u = U + sum_i c_i s_i / KF + F/2 (the velocity part e_i(U) of the
+  // stored deviations carries momentum U and no other first moment).
+  constexpr bool V2 = Cfg::V2;
+  constexpr int FQ = V2 ? Q + D : Q;
+  auto fill_store = [&](int e, bool ok, int mm, int gx, int gy, const R (&fv)[FQ], int q) {
     R u[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) u[a] = R(0);
@@ -512,20 +579,35 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 #pragma unroll
         for (int a = 0; a < D; ++a) F[a] += ph.fdiv[(uint32_t)a * P32 + sf];
       }
-      velocity<L, R>(fv, F, u);
+      if constexpr (V2) {
+        R fq[Q], z3[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fq[i] = fv[i];
+        velocity<L, R>(fq, z3, u);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          u[a] = u[a] * R(1.0f / Store<S>::KF) + fv[Q + a] + R(0.5) * F[a];
+      } else {
+        velocity<L, R>(fv, F, u);
+      }
     }
     Vel<R, D> t;
 #pragma unroll
     for (int a = 0; a < (D == 3 ? 4 : 2); ++a) t.v[a] = a < D ? u[a] : R(0);
     ring[slot(q)][e] = t;
   };
-  auto fill_load = [&](bool ok, int mm, int gx, int gy, R (&fv)[Q]) {
+  auto fill_load = [&](bool ok, int mm, int gx, int gy, R (&fv)[FQ]) {
     if (ok) {
       // 32-bit offsets (Q * pitch < 2^32)
       const uint32_t s = (D == 3) ? ((uint32_t)mm * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx
                                   : (uint32_t)mm * (uint32_t)nx + (uint32_t)gx;
 #pragma unroll
       for (int i = 0; i < Q; ++i) fv[i] = Store<S>::ld(b.f_in + ((uint32_t)i * P32 + s));
+      if constexpr (V2) {
+        const float* U = f_ext<L>(b.f_in, P);
+#pragma unroll
+        for (int a = 0; a < D; ++a) fv[Q + a] = __ldg(U + ((uint32_t)a * P32 + s));
+      }
     }
   };
   // ring slot e of plane q, whose node (gx, gy) the caller found (`has`)
@@ -533,7 +615,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     if (e >= NE) return;
     const int mm = plane_of(q);
     const bool ok = has && mm >= 0;
-    R fv[Q];
+    R fv[FQ];
     fill_load(ok, mm, gx, gy, fv);
     fill_store(e, ok, mm, gx, gy, fv, q);
   };
@@ -566,7 +648,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       fill(e, shas[t], sgx[t], sgy[t], m0);
       fill(e, shas[t], sgx[t], sgy[t], m0 + 1);
     }
-    R fv[SPF ? SPF : 1][Q];
+    R fv[SPF ? SPF : 1][FQ];
     int mq = plane_of(m0 + 2);
     if (m0 + 2 <= m1) {
 #pragma unroll
@@ -652,7 +734,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if (wide_n(n)) {
             constexpr int CPR = 32 / EPC;          // chunks per row of 32 nodes
             constexpr int NCP = NPP * CPR;         // population chunks
-            constexpr int NCH = NCP + 32 * 4 / 16; // and chi (4-byte) chunks
+            constexpr int NCX = NCP + 32 * 4 / 16; // and chi (4-byte) chunks
+            constexpr int NCH = NCX + (V2 ? 8 * (1 + D) : 0);  // and h0, U (16-bit forms)
             const uint32_t s0 = sq32 - (uint32_t)lane;  // node of lane 0
             const int wb = col - lane;             // the row's stage columns
 #pragma unroll
@@ -662,10 +745,17 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                 const int v = c / CPR, sub = c % CPR;
                 const int i = v < Q ? v : k + (v - Q) * C;
                 const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + s0 + (uint32_t)(sub * EPC));
-                if (i < Q) cp_async<16>(&stage[st][v][wb + sub * EPC], src);
-              } else if (c < NCH) {
+                // (16-bit forms: the rest stress population is in FP32)
+                if (i < Q && !(V2 && v == 0)) cp_async<16>(&stage[st][v][wb + sub * EPC], src);
+              } else if (c < NCX) {
                 const int sub = c - NCP;
                 cp_async<16>(&stage_x[st][wb + sub * 4], b.chi + ((uint32_t)k * P32 + s0 + (uint32_t)(sub * 4)));
+              } else if (V2 && c < NCH) {
+                const int arr = (c - NCX) >> 3, sub = (c - NCX) & 7;
+                const float* src = arr == 0 ? h_ext<L>(b.h_in, P) + (uint32_t)k * P32
+                                            : f_ext<L>(b.f_in, P) + (uint32_t)(arr - 1) * P32;
+                if constexpr (V2)
+                  cp_async<16>(&stage_e[st][arr][wb + sub * 4], src + s0 + (uint32_t)(sub * 4));
               }
             }
             continue;
@@ -680,7 +770,13 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
               const int v = 2 * jj + par;
               const int i = v < Q ? v : k + (v - Q) * C;
               const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + sp);
-              if (v < NPP && i < Q) cp_async<4>(&stage[st][v][tb], src);
+              if (v < NPP && i < Q && !(V2 && v == 0)) cp_async<4>(&stage[st][v][tb], src);
+            }
+            if constexpr (V2) {   // the FP32 values of this lane's own node
+              cp_async<4>(&stage_e[st][0][col], h_ext<L>(b.h_in, P) + ((uint32_t)k * P32 + sq32));
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+                cp_async<4>(&stage_e[st][1 + a][col], f_ext<L>(b.f_in, P) + ((uint32_t)a * P32 + sq32));
             }
           } else {
 #pragma unroll
@@ -716,12 +812,17 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     const int mn = plane_of(m + 1);
     const bool fslot = !FW && tid < NE;
     const bool fok = fslot && slot_node(tid, fgx, fgy) && mn >= 0;
-    R fn[FW ? 1 : Q];
+    R fn[FW ? 1 : FQ];
     if (!FW && fok) {
       const long long sn = (D == 3) ? ((long long)mn * ny + fgy) * nx + fgx
                                     : (long long)mn * nx + fgx;
 #pragma unroll
       for (int i = 0; i < (FW ? 1 : Q); ++i) fn[i] = Store<S>::ld(b.f_in + i * P + sn);
+      if constexpr (V2 && !FW) {
+        const float* U = f_ext<L>(b.f_in, P);
+#pragma unroll
+        for (int a = 0; a < D; ++a) fn[Q + a] = __ldg(U + a * P + sn);
+      }
     }
     // Staged storage types keep this plane's values in stage buffer st
     // until the collision has used them (read there again rather than held
@@ -753,13 +854,19 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
             const int col = tid + n * WC;
             const uint32_t sn32 = s32 + 32u * n;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) stage[st][i][col] = hin_k[(uint32_t)i * P32 + sn32];
+            for (int i = V2 ? 1 : 0; i < Q; ++i) stage[st][i][col] = hin_k[(uint32_t)i * P32 + sn32];
 #pragma unroll
             for (int j = 0; j < NFM; ++j) {
               const int i = k + j * C;
               if (i < Q) stage[st][Q + j][col] = b.f_in[(uint32_t)i * P32 + sn32];
             }
             stage_x[st][col] = b.chi[(uint32_t)k * P32 + sn32];
+            if constexpr (V2) {
+              stage_e[st][0][col] = h_ext<L>(b.h_in, P)[(uint32_t)k * P32 + sn32];
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+                stage_e[st][1 + a][col] = f_ext<L>(b.f_in, P)[(uint32_t)a * P32 + sn32];
+            }
           }
         }
 #pragma unroll
@@ -767,13 +874,18 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if (!active_n(n)) continue;
           const int col = tid + n * WC;
           R a = R(0), psum = R(0);
+          if constexpr (V2) a = stage_e[st][0][col];
+          else a = Store<S>::cvt(stage[st][0][col]);
 #pragma unroll
-          for (int i = 0; i < Q; ++i) a += Store<S>::cvt(stage[st][i][col]);
+          for (int i = 1; i < Q; ++i) a += Store<S>::cvt(stage[st][i][col]);
 #pragma unroll
           for (int j = 0; j < NFM; ++j) {
             const int i = k + j * C;
             if (i != 0 && i < Q) psum += Store<S>::cvt(stage[st][Q + j][col]);
           }
+          // (16-bit forms: the sum of the scaled deviations s_i, i != 0;
+          // the collision adds the sum of e_i(U), i != 0, = 1.5 w_0 |U|^2)
+          if constexpr (V2) psum *= R(1.0f / Store<S>::KF);
           sAd[m & (NBUF - 1)][node + 32 * n][k] = a;
           sPf[m & (NBUF - 1)][node + 32 * n][k] = psum;
         }
@@ -803,15 +915,17 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     }
     __syncthreads();                    // A
 
-    // ---- learned closure: one warp per group evaluates the network -------------
+    // ---- learned closure: two warps per group evaluate the network, each for
+    // the 16 nodes of one m16 tile (lanes 16 k .. 16 k + 15 of warp k) -------
     if constexpr (CL) {
-      if (k == 0) {
+      if (k < 2) {
         constexpr int IN = MlpDims<D>::IN;
+        const bool mine = (lane >> 4) == k;   // this lane's node is in warp k's tile
         float xin[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) xin[q] = 0.f;
         R gr[D][D], Ad[C], A[C];
-        if (active) {
+        if (active && mine) {
 #pragma unroll
           for (int bq = 0; bq < D; ++bq) {
             const R uo = ring[rc][e_own].v[bq];
@@ -852,14 +966,16 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if (D == 2) xin[q++] = float(ph.inv_lam);
           (void)IN;
         }
+        if (mine) {
 #pragma unroll
-        for (int q = 0; q < 16; q += 2)
-          *reinterpret_cast<uint32_t*>(&cls.X[grp][lane][q]) = pack_bf16x2(xin[q], xin[q + 1]);
+          for (int q = 0; q < 16; q += 2)
+            *reinterpret_cast<uint32_t*>(&cls.X[grp][lane][q]) = pack_bf16x2(xin[q], xin[q + 1]);
+        }
         __syncwarp();
-        mlp_warp(cls.P, cls.X[grp], cls.Y[grp]);
+        mlp_tile(cls.P, cls.X[grp], cls.Y[grp], k);
         __syncwarp();
         bool used = false;
-        if (active) {
+        if (active && mine) {
           R chi_an[C];
           chi_tensor<L, R>(A, Ad, gr, ph, chi_an);
           float num = 0.f, den = 0.f;
@@ -876,7 +992,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 #pragma unroll
           for (int c = 0; c < C; ++c) cls.chi[c][node] = used ? chi_nn[c] : float(chi_an[c]);
         }
-        const unsigned act = __ballot_sync(0xffffffffu, active);
+        const unsigned act = __ballot_sync(0xffffffffu, active && mine);
         const unsigned use = __ballot_sync(0xffffffffu, used);
         if (lane == 0 && ph.cl_count && act) {
           atomicAdd(ph.cl_count, (unsigned long long)__popc(use));
@@ -909,6 +1025,18 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         lds_row<R, C>(&sPf[m & (NBUF - 1)][nd][0], pf);
 #pragma unroll
         for (int q = 0; q < C; ++q) sumf += pf[q];
+      }
+      // 16-bit forms: the node's stored velocity U (the reference of its
+      // flow populations), and the sum of e_i(U) over i != 0
+      R Us[V2 ? D : 1];
+      if constexpr (V2) {
+        R UU = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          Us[a] = stage_e[st][1 + a][col];
+          UU += Us[a] * Us[a];
+        }
+        sumf += R(1.5 * L::w(0)) * UU;
       }
       R F[3];
       body_force<L, R>(ph, xn, D == 3 ? y : m, F);
@@ -1040,19 +1168,48 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       const R alpha = om * Ad_k + src;
       const R beta = R(3) * (om * A_k + ph.kh * src);
       const R keep = R(1) - om;
+      if constexpr (V2) {
+        // this node's velocity: the reference of the flow populations it
+        // receives for the next step (component threads k < D write one each)
+        if (k < D) {
+          const R uk = k == 0 ? u[0] : (k == 1 ? u[1] : u[D - 1]);
+          f_ext<L>(b.f_out, P)[(uint32_t)k * P32 + sn32] = float(uk);
+        }
+      }
+      // velocity of the node that receives population i: the ring holds the
+      // tile's neighbours (periodic images included); through a wall the
+      // population comes back to this node
+      auto dest_u = [&](int i, bool bounced, R (&ud)[D]) {
+        if (bounced) {
+#pragma unroll
+          for (int a = 0; a < D; ++a) ud[a] = u[a];
+          return;
+        }
+        const int cm = D == 3 ? L::cz(i) : L::cy(i);
+        const int rs = cm == 1 ? rp : (cm == -1 ? rm : rc);
+        const int es = eo + L::cx(i) + (D == 3 ? L::cy(i) * EX : 0);
+        const Vel<R, D> t = ring[rs][es];
+#pragma unroll
+        for (int a = 0; a < D; ++a) ud[a] = t.v[a];
+      };
       auto emit = [&](auto FASTC) {
         constexpr bool FAST = decltype(FASTC)::value;
-        auto index = [&](int i) -> uint32_t {
+        // offset of the slot that receives population i; `bounced`: through
+        // a wall, back to this node (the slot's direction is then opp(i))
+        auto index = [&](int i, bool& bounced) -> uint32_t {
           if constexpr (FAST) {
+            bounced = false;
             const int cx = L::cx(i);
             const uint32_t xw = cx == 1 ? wxp : (cx == -1 ? wxm : 0u);
             return sn32 + (uint32_t)i * P32 + (uint32_t)(cx + L::cy(i) * nx + L::cz(i) * strm) + xw;
           } else {
             int j;
             const uint32_t d = dest(i, j);
+            bounced = j != i;
             return (uint32_t)j * P32 + d;
           }
         };
+        R h0post = R(0), hres = R(0);   // 16-bit forms: rest population, residuals
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           R cu = R(0);
@@ -1063,12 +1220,28 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
             if (c == -1) cu -= u[a];
           }
           R hvi;
-          if constexpr (PF) hvi = Store<S>::cvt(stage[st][i][col]);
-          else hvi = hv[i];
+          if constexpr (PF) {
+            if constexpr (V2) hvi = i == 0 ? R(stage_e[st][0][col]) : Store<S>::cvt(stage[st][i][col]);
+            else hvi = Store<S>::cvt(stage[st][i][col]);
+          } else {
+            hvi = hv[i];
+          }
           const R wa = R(L::w(i)) * alpha, wb = R(L::w(i)) * beta;
           const R post = keep * hvi + (wa + cu * wb);
-          Store<S>::st(hout_k + index(i), post, Store<S>::sr ? lcg_next(rng) : 0u);
+          if constexpr (V2) {
+            if (i == 0) {
+              h0post = post;
+            } else {
+              bool bnc;
+              const uint32_t o = index(i, bnc);
+              hres += post - Store<S>::st_r(hout_k + o, post, Store<S>::sr ? lcg_next(rng) : 0u);
+            }
+          } else {
+            bool bnc;
+            Store<S>::st(hout_k + index(i, bnc), post, Store<S>::sr ? lcg_next(rng) : 0u);
+          }
         }
+        if constexpr (V2) h_ext<L>(b.h_out, P)[(uint32_t)k * P32 + sn32] = float(h0post + hres);
 
         // f_i, i = k (mod C): f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
         on_component(k, [&](auto KC) {
@@ -1093,8 +1266,20 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
               R foi;
               if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][col]);
               else foi = fo[jj];
+              if constexpr (V2) foi = foi * R(1.0f / Store<S>::KF) + feq_u<L, R>(i, Us);
               const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
-              Store<S>::st(b.f_out + index(i), post, Store<S>::sr ? lcg_next(rng) : 0u);
+              bool bnc;
+              const uint32_t o = index(i, bnc);
+              if constexpr (V2) {
+                // scaled deviation from e_j(u) of the receiving node
+                R ud[D];
+                dest_u(i, bnc, ud);
+                const R ej = feq_u<L, R>(bnc ? L::opp(i) : i, ud);
+                Store<S>::st(b.f_out + o, R(Store<S>::KF) * (post - ej),
+                             Store<S>::sr ? lcg_next(rng) : 0u);
+              } else {
+                Store<S>::st(b.f_out + o, post, Store<S>::sr ? lcg_next(rng) : 0u);
+              }
             }
           }
         });
@@ -1323,7 +1508,7 @@ __global__ void k_collide_split(Grid g, Phys<RT<S>> ph, Bufs<S> b,
       F[1] += dv[1];
       F[2] += dv[2];
     }
-    collide_site<L, S, HOLD_H, ORIG>(g, ph, b, s, x, y, z, u, gr, fv, F);
+    collide_site<L, S, HOLD_H, ORIG>(g, ph, b, s, x, y, z, u, gr, fv, F, ubuf);
   }
 }
 
@@ -1352,6 +1537,9 @@ __global__ void k_init(Grid g, S* __restrict__ f, S* __restrict__ h,
     for (int k = 0; k < C; ++k)
       A[k] = A0 ? R(A0[s * C + k]) : (L::ca(k) == L::cb(k) ? R(1) : R(0));
     const R p = p0 ? R(p0[s]) : R(0);
+    R hres[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) hres[k] = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       R cu = R(0);
@@ -1359,13 +1547,34 @@ __global__ void k_init(Grid g, S* __restrict__ f, S* __restrict__ h,
       for (int a = 0; a < D; ++a) cu += R(cc<L>(i, a)) * u[a];
       const R wi = R(L::w(i));
       const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
-      Store<S>::st(f + i * P + s, lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu),
-                   0x80000000u);
+      if constexpr (Store<S>::V2) {
+        // f^eq(p, u) - e_i(u) = lam_i p, scaled; U = u
+        Store<S>::st(f + i * P + s, R(Store<S>::KF) * (lam_i * p), 0x80000000u);
+      } else {
+        Store<S>::st(f + i * P + s, lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu),
+                     0x80000000u);
+      }
 #pragma unroll
-      for (int k = 0; k < C; ++k)
-        store_h<L, S>(h, P, s, k, i,
-                      wi * ((A[k] - (diag<L>(k) ? R(1) : R(0))) + A[k] * (R(3) * cu)),
-                      0x80000000u);
+      for (int k = 0; k < C; ++k) {
+        const R v = wi * ((A[k] - (diag<L>(k) ? R(1) : R(0))) + A[k] * (R(3) * cu));
+        if constexpr (Store<S>::V2) {
+          if (i > 0) hres[k] += v - Store<S>::st_r(h + (long long)(k * Q + i) * P + s, v, 0x80000000u);
+        } else {
+          store_h<L, S>(h, P, s, k, i, v, 0x80000000u);
+        }
+      }
+    }
+    if constexpr (Store<S>::V2) {
+      float* U = f_ext<L>(f, P);
+      float* h0 = h_ext<L>(h, P);
+#pragma unroll
+      for (int a = 0; a < D; ++a) U[a * P + s] = float(u[a]);
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        R cu0 = R(0);
+        const R v0 = R(L::w(0)) * ((A[k] - (diag<L>(k) ? R(1) : R(0))) + A[k] * (R(3) * cu0));
+        h0[k * P + s] = float(v0 + hres[k]);
+      }
     }
 #pragma unroll
     for (int k = 0; k < C; ++k) chi[k * P + s] = 0;
@@ -1684,6 +1893,133 @@ static __global__ void __launch_bounds__(kReduceThreads)
     out[0] = sm[0][0];
     out[1] = sm[0][1];
     out[2] = sm[0][2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// High-Wi repair of the conformation (fvlb_repair_conformation).  Per node,
+// in FP64: A from the stress populations, its eigen-decomposition by cyclic
+// Jacobi rotations with the rotations accumulated into the eigenvectors
+// (ten sweeps), and where the smallest eigenvalue is below eps,
+// A' = V max(Lambda, eps) V^T, applied as h'_{k,i} += w_i (A' - A)_k, which
+// moves the zeroth moment of h only (sum_i w_i c_i = 0).  16-bit forms: the
+// 16-bit populations are re-rounded and their rounding residual goes to the
+// FP32 rest population, as in the step.  count[0] += nodes changed (a node
+// with a non-finite A is counted and left as it is).
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void jacobi_eig(double (&a)[3][3], double (&v)[3][3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[r][c] = r == c ? 1.0 : 0.0;
+#pragma unroll 1
+  for (int sweep = 0; sweep < 10; ++sweep) {
+#pragma unroll
+    for (int pr = 0; pr < (D == 3 ? 3 : 1); ++pr) {
+      const int p = pr == 2 ? 1 : 0, q = pr == 0 ? 1 : 2;
+      const double apq = a[p][q];
+      if (apq == 0.0) continue;
+      const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+      const double t = copysign(1.0, th) / (fabs(th) + hypot(th, 1.0));
+      const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+      // a <- J^T a J and v <- v J for the rotation J in the (p, q) plane
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double akp = a[k][p], akq = a[k][q];
+        a[k][p] = c * akp - sn * akq;
+        a[k][q] = sn * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double apk = a[p][k], aqk = a[q][k];
+        a[p][k] = c * apk - sn * aqk;
+        a[q][k] = sn * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double vkp = v[k][p], vkq = v[k][q];
+        v[k][p] = c * vkp - sn * vkq;
+        v[k][q] = sn * vkp + c * vkq;
+      }
+    }
+  }
+}
+
+template <class L, class S>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_repair(Grid g, S* __restrict__ h, double eps, unsigned long long* __restrict__ count,
+             long long N) {
+  using R = RT<S>;
+  constexpr int D = L::D, Q = L::Q, C = L::C;
+  const long long P = g.pitch;
+  unsigned long long mine = 0;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+       s += (long long)gridDim.x * blockDim.x) {
+    double M[C];
+    bool fin = true;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) acc += double(load_h<L, S>(h, P, s, k, i));
+      M[k] = acc;
+      fin &= isfinite(acc);
+    }
+    if (!fin) {
+      ++mine;
+      continue;
+    }
+    double a[3][3], v[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        a[r][c] = (r < D && c < D) ? M[sym<L>(r, c)] + (r == c ? 1.0 : 0.0) : 0.0;
+    jacobi_eig<D>(a, v);
+    double lmin = a[0][0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) lmin = fmin(lmin, a[k][k]);
+    if (!(lmin < eps)) continue;
+    ++mine;
+    double dA[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const int ra = L::ca(k), rb = L::cb(k);
+      double An = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) An += v[ra][j] * fmax(a[j][j], eps) * v[rb][j];
+      dA[k] = An - (M[k] + (ra == rb ? 1.0 : 0.0));
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      R res = R(0);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        S* q = h + (long long)(k * Q + i) * P + s;
+        const R nv = R(double(Store<S>::cvt(*q)) + L::w(i) * dA[k]);
+        if constexpr (Store<S>::V2) res += nv - Store<S>::st_r(q, nv, 0x80000000u);
+        else Store<S>::st(q, nv, 0u);
+      }
+      if constexpr (Store<S>::V2) {
+        float* h0 = h_ext<L>(h, P) + k * P + s;
+        *h0 = float(double(*h0) + L::w(0) * dA[k] + double(res));
+      } else {
+        S* q = h + (long long)(k * Q) * P + s;
+        Store<S>::st(q, R(double(Store<S>::cvt(*q)) + L::w(0) * dA[k]), 0u);
+      }
+    }
+  }
+  // block total, then one atomic per block (an integer sum: order-free)
+  __shared__ unsigned long long sm[kReduceThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kReduceThreads / 32; ++w) t += sm[w];
+    if (t) atomicAdd(count, t);
   }
 }
 

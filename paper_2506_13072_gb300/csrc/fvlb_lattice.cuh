@@ -7,6 +7,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace fvlb {
 
 // ---------------------------------------------------------------------------
@@ -103,6 +105,7 @@ template <>
 struct Store<double> {
   using R = double;     // arithmetic
   using X = double;     // chi of the previous step
+  static constexpr bool V2 = false;  // no reference-based 16-bit layout (see below)
   __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double cvt(double v) { return v; }
   static constexpr bool sr = false;
@@ -118,6 +121,7 @@ template <>
 struct Store<float> {
   using R = float;
   using X = float;
+  static constexpr bool V2 = false;
   __device__ static __forceinline__ float ld(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float cvt(float v) { return v; }
   static constexpr bool sr = false;
@@ -133,6 +137,8 @@ template <>
 struct Store<__half> {
   using R = float;
   using X = float;
+  static constexpr bool V2 = true;
+  static constexpr float KF = 4096.0f;       // flow-population scale (2^12)
   static constexpr bool sr = false;
   __device__ static __forceinline__ float ld(const __half* p) {
     return __half2float(__ldg(p));
@@ -140,6 +146,12 @@ struct Store<__half> {
   __device__ static __forceinline__ float cvt(__half v) { return __half2float(v); }
   __device__ static __forceinline__ void st(__half* p, float v, uint32_t) {
     *p = __float2half_rn(v);
+  }
+  // store, and return the stored value
+  __device__ static __forceinline__ float st_r(__half* p, float v, uint32_t) {
+    const __half q = __float2half_rn(v);
+    *p = q;
+    return __half2float(q);
   }
   __device__ static __forceinline__ float ld_l2(const __half* p) {
     return __half2float(__ushort_as_half(ld_l2_u16(p)));
@@ -150,6 +162,8 @@ template <>
 struct Store<__nv_bfloat16> {
   using R = float;
   using X = float;
+  static constexpr bool V2 = true;
+  static constexpr float KF = 1.0f;          // (no subnormal range to avoid)
   static constexpr bool sr = false;
   __device__ static __forceinline__ float ld(const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(p));
@@ -157,6 +171,11 @@ struct Store<__nv_bfloat16> {
   __device__ static __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, uint32_t) {
     *p = __float2bfloat16_rn(v);
+  }
+  __device__ static __forceinline__ float st_r(__nv_bfloat16* p, float v, uint32_t) {
+    const __nv_bfloat16 q = __float2bfloat16_rn(v);
+    *p = q;
+    return __bfloat162float(q);
   }
   __device__ static __forceinline__ float ld_l2(const __nv_bfloat16* p) {
     return __uint_as_float((uint32_t)ld_l2_u16(p) << 16);
@@ -179,6 +198,8 @@ template <>
 struct Store<half_sr> {
   using R = float;
   using X = float;
+  static constexpr bool V2 = true;
+  static constexpr float KF = 4096.0f;
   static constexpr bool sr = true;
   __device__ static __forceinline__ float ld(const half_sr* p) {
     return __half2float(__ushort_as_half(__ldg(&p->b)));
@@ -187,14 +208,22 @@ struct Store<half_sr> {
     return __half2float(__ushort_as_half(v.b));
   }
   // r: 32 random bits.  Add r * ulp(|v|) in magnitude, then truncate.
-  __device__ static __forceinline__ void st(half_sr* p, float v, uint32_t r) {
+  __device__ static __forceinline__ __half round(float v, uint32_t r) {
     const uint32_t bits = __float_as_uint(v);
     int e = (int)((bits >> 23) & 0xffu) - 127;  // binade of |v|
     e = e < -14 ? -14 : e;                      // half subnormals share one ulp
     const float ulp = __uint_as_float((uint32_t)(e - 10 + 127) << 23);
     const float jit = __uint2float_rz(r >> 8) * (1.0f / 16777216.0f) * ulp;
     const float w = v + copysignf(jit, v);
-    p->b = __half_as_ushort(__float2half_rz(w));
+    return __float2half_rz(w);
+  }
+  __device__ static __forceinline__ void st(half_sr* p, float v, uint32_t r) {
+    p->b = __half_as_ushort(round(v, r));
+  }
+  __device__ static __forceinline__ float st_r(half_sr* p, float v, uint32_t r) {
+    const __half q = round(v, r);
+    p->b = __half_as_ushort(q);
+    return __half2float(q);
   }
   __device__ static __forceinline__ float ld_l2(const half_sr* p) {
     return __half2float(__ushort_as_half(ld_l2_u16(p)));
@@ -205,6 +234,8 @@ template <>
 struct Store<bf16_sr> {
   using R = float;
   using X = float;
+  static constexpr bool V2 = true;
+  static constexpr float KF = 1.0f;
   static constexpr bool sr = true;
   __device__ static __forceinline__ float ld(const bf16_sr* p) {
     return __uint_as_float((uint32_t)__ldg(&p->b) << 16);
@@ -217,6 +248,13 @@ struct Store<bf16_sr> {
     const uint32_t exp = bits & 0x7f800000u;
     const uint32_t out = exp == 0x7f800000u ? bits : bits + (r >> 16);
     p->b = (unsigned short)(out >> 16);
+  }
+  __device__ static __forceinline__ float st_r(bf16_sr* p, float v, uint32_t r) {
+    const uint32_t bits = __float_as_uint(v);
+    const uint32_t exp = bits & 0x7f800000u;
+    const uint32_t out = (exp == 0x7f800000u ? bits : bits + (r >> 16)) & 0xffff0000u;
+    p->b = (unsigned short)(out >> 16);
+    return __uint_as_float(out);
   }
   __device__ static __forceinline__ float ld_l2(const bf16_sr* p) {
     return __uint_as_float((uint32_t)ld_l2_u16(p) << 16);
@@ -286,6 +324,58 @@ struct Bufs {
   S* __restrict__ h_out;
   X* __restrict__ chi;  // [C][pitch], read and rewritten in place
 };
+
+// ---------------------------------------------------------------------------
+// Layout of the 16-bit forms (Store<S>::V2).  Rounding a population to 16
+// bits every step biases slowly evolving flows: the per-step change of a
+// population can be as small as its rounding error, which then accumulates
+// coherently.  So:
+//  - the flow populations are stored scaled, s_i = KF (f_i - e_i(U)), as
+//    deviations from the velocity part of the equilibrium,
+//    e_i(U) = w_i (3 c_i.U + 4.5 (c_i.U)^2 - 1.5 U.U), at the velocity U
+//    that their destination node had in the step that wrote them (a node
+//    pushing f_i to x + c_i takes U = u(x + c_i) from its velocity ring);
+//    U[D][pitch] (FP32) follows f[Q][pitch] in the same buffer, written by
+//    each node for its own populations of the next step;
+//  - the stress populations h'_{k,i} (i >= 1) are 16-bit; the rest
+//    population of each component is FP32, h0[C][pitch] following
+//    h[C][Q][pitch] (whose i = 0 slots are unused), and takes up the
+//    rounding residual of the component's other populations at every
+//    store, so the stored populations of a node carry no rounding bias in
+//    their sum.
+// ---------------------------------------------------------------------------
+template <class S>
+struct V2Layout {
+  static constexpr bool on = Store<S>::V2;
+};
+
+// velocity part of f^eq: e_i(u) = w_i (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+template <class L, class R>
+__device__ __forceinline__ R feq_u(int i, const R (&u)[L::D]) {
+  R cu = R(0), uu = R(0);
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    const int c = cc<L>(i, a);
+    if (c == 1) cu += u[a];
+    if (c == -1) cu -= u[a];
+    uu += u[a] * u[a];
+  }
+  return R(L::w(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+}
+
+// The FP32 arrays that follow the 16-bit populations: U[D][pitch] after
+// f[Q][pitch], h0[C][pitch] after h[C][Q][pitch] (pitch is a multiple of 64
+// elements, so they start 128-byte aligned).
+template <class L, class T>
+__device__ __forceinline__ auto f_ext(T* f, long long pitch) {
+  using F = typename std::conditional<std::is_const<T>::value, const float, float>::type;
+  return reinterpret_cast<F*>(f + (long long)L::Q * pitch);
+}
+template <class L, class T>
+__device__ __forceinline__ auto h_ext(T* h, long long pitch) {
+  using F = typename std::conditional<std::is_const<T>::value, const float, float>::type;
+  return reinterpret_cast<F*>(h + (long long)L::C * L::Q * pitch);
+}
 
 // ---------------------------------------------------------------------------
 // Per-site algebra.

@@ -118,9 +118,9 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
   if constexpr (std::is_same<S, float>::value && XN == 1 && !ORIG) {
-    if (d.mlp) {  // learned closure (FP32 storage only); one block per SM
-      if (d.walls) return launch_kernel<L, S, GX, TY, 1, true, FW, true, 1>(grid, d, g, ph, b, mchunk);
-      return launch_kernel<L, S, GX, TY, 1, false, FW, true, 1>(grid, d, g, ph, b, mchunk);
+    if (d.mlp) {  // learned closure (FP32 storage only); two blocks per SM
+      if (d.walls) return launch_kernel<L, S, GX, TY, 2, true, FW, true, 1>(grid, d, g, ph, b, mchunk);
+      return launch_kernel<L, S, GX, TY, 2, false, FW, true, 1>(grid, d, g, ph, b, mchunk);
     }
   }
   if (d.walls)
@@ -261,6 +261,16 @@ cudaError_t conf_impl(const StepDesc& d, double* part, double* out) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_conf_final<<<1, kReduceThreads, 0, d.stream>>>(part, nparts, out);
+  return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t repair_impl(const StepDesc& d, double eps, unsigned long long* count) {
+  Grid g{d.nx, d.ny, L::D == 3 ? d.nz : 1, d.walls, d.pitch};
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), d.stream);
+  if (e != cudaSuccess) return e;
+  k_repair<L, S><<<grid_stride_blocks(d.N, kReduceThreads, d.sms), kReduceThreads, 0, d.stream>>>(
+      g, static_cast<S*>(const_cast<void*>(d.h_in)), eps, count, d.N);
   return cudaGetLastError();
 }
 

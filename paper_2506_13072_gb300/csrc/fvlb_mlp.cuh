@@ -9,10 +9,11 @@
 // CUDA cores, deterministic block reductions, Adam); inference packs the
 // weights to BF16 and runs each layer of 32 nodes on the tensor cores with
 // mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  The products are
-// 32 x 16 x 64 and 32 x 64 x 64 per warp, fused into the collision of the
-// nodes that a warp already holds in registers; the register-level mma keeps
-// them there (a tcgen05 tile would need the operands staged through shared
-// memory and tensor memory for a 32-row product).
+// 16 x 16 x 64 and 16 x 64 x 64 per warp (two warps per 32-node group, one
+// m16 tile each), fused into the collision of the nodes the group already
+// holds; the register-level mma keeps them there (a tcgen05 tile would need
+// the operands staged through shared memory and tensor memory for a 16-row
+// product).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -78,67 +79,80 @@ __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// One warp: Y[r][0..7] = MLP(X[r][0..15]) for the 32 rows r.  X and Y are
-// the warp's own shared-memory staging rows; P the packed weights.
+// One warp: Y[r][0..7] = MLP(X[r][0..15]) for the 16 rows r of m-tile mt
+// (rows 16 mt .. 16 mt + 15).  X and Y are shared-memory staging rows; P
+// the packed weights.
 // Fragment layout of mma.m16n8k16 (g = lane / 4, t = lane % 4):
 //   A: a0 (g, 2t..2t+1) a1 (g+8, 2t..) a2 (g, 2t+8..) a3 (g+8, 2t+8..)
 //   B: b0 (k = 2t..2t+1, n = g)  b1 (k = 2t+8.., n = g)
 //   C: c0,c1 (g, 2t..2t+1)  c2,c3 (g+8, 2t..2t+1)
 // The accumulators of two adjacent n8 tiles form the A fragment of the
-// next layer's k16 tile, so hidden activations never leave registers.
-__device__ __forceinline__ void mlp_warp(const MlpPacked& P, const __nv_bfloat16 (*X)[24],
-                                         float (*Y)[8]) {
+// next layer's k16 tile, so hidden activations never leave registers; the
+// layers are interleaved so that only one layer-1 output (16 registers of
+// packed BF16) and one pair of layer-2 tiles are live at a time.
+__device__ __forceinline__ void mlp_tile(const MlpPacked& P, const __nv_bfloat16 (*X)[24],
+                                         float (*Y)[8], int mt) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
+  const int r0 = mt * 16 + g, r1 = r0 + 8;
+  uint32_t a[4] = {lds32(&X[r0][2 * t]), lds32(&X[r1][2 * t]), lds32(&X[r0][2 * t + 8]),
+                   lds32(&X[r1][2 * t + 8])};
+  // layer 1: 16 -> 64, packed k-tile by k-tile into layer 2's A fragments
+  uint32_t a2[4][4];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const int r0 = mt * 16 + g, r1 = r0 + 8;
-    uint32_t a[4] = {lds32(&X[r0][2 * t]), lds32(&X[r1][2 * t]), lds32(&X[r0][2 * t + 8]),
-                     lds32(&X[r1][2 * t + 8])};
-    // layer 1: 16 -> 64
-    float h[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const float c0 = P.b1[nt * 8 + 2 * t], c1 = P.b1[nt * 8 + 2 * t + 1];
-      h[nt][0] = c0; h[nt][1] = c1; h[nt][2] = c0; h[nt][3] = c1;
-      mma_16816(h[nt], a, lds32(&P.W1[nt * 8 + g][2 * t]), lds32(&P.W1[nt * 8 + g][2 * t + 8]));
+  for (int kt = 0; kt < 4; ++kt) {
+    float h0[4], h1[4];
+    {
+      const float c0 = P.b1[2 * kt * 8 + 2 * t], c1 = P.b1[2 * kt * 8 + 2 * t + 1];
+      h0[0] = c0; h0[1] = c1; h0[2] = c0; h0[3] = c1;
+      const float d0 = P.b1[(2 * kt + 1) * 8 + 2 * t], d1 = P.b1[(2 * kt + 1) * 8 + 2 * t + 1];
+      h1[0] = d0; h1[1] = d1; h1[2] = d0; h1[3] = d1;
     }
-    uint32_t a2[4][4];
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-      a2[kt][0] = pack_bf16x2(gelu_fast(h[2 * kt][0]), gelu_fast(h[2 * kt][1]));
-      a2[kt][1] = pack_bf16x2(gelu_fast(h[2 * kt][2]), gelu_fast(h[2 * kt][3]));
-      a2[kt][2] = pack_bf16x2(gelu_fast(h[2 * kt + 1][0]), gelu_fast(h[2 * kt + 1][1]));
-      a2[kt][3] = pack_bf16x2(gelu_fast(h[2 * kt + 1][2]), gelu_fast(h[2 * kt + 1][3]));
-    }
-    // layer 2: 64 -> 64
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const float c0 = P.b2[nt * 8 + 2 * t], c1 = P.b2[nt * 8 + 2 * t + 1];
-      h[nt][0] = c0; h[nt][1] = c1; h[nt][2] = c0; h[nt][3] = c1;
-#pragma unroll
-      for (int kt = 0; kt < 4; ++kt)
-        mma_16816(h[nt], a2[kt], lds32(&P.W2[nt * 8 + g][kt * 16 + 2 * t]),
-                  lds32(&P.W2[nt * 8 + g][kt * 16 + 2 * t + 8]));
-    }
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-      a2[kt][0] = pack_bf16x2(gelu_fast(h[2 * kt][0]), gelu_fast(h[2 * kt][1]));
-      a2[kt][1] = pack_bf16x2(gelu_fast(h[2 * kt][2]), gelu_fast(h[2 * kt][3]));
-      a2[kt][2] = pack_bf16x2(gelu_fast(h[2 * kt + 1][0]), gelu_fast(h[2 * kt + 1][1]));
-      a2[kt][3] = pack_bf16x2(gelu_fast(h[2 * kt + 1][2]), gelu_fast(h[2 * kt + 1][3]));
-    }
-    // layer 3: 64 -> 8 (OUT used)
-    float y[4];
-    y[0] = P.b3[2 * t]; y[1] = P.b3[2 * t + 1]; y[2] = y[0]; y[3] = y[1];
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt)
-      mma_16816(y, a2[kt], lds32(&P.W3[g][kt * 16 + 2 * t]), lds32(&P.W3[g][kt * 16 + 2 * t + 8]));
-    Y[r0][2 * t] = y[0];
-    Y[r0][2 * t + 1] = y[1];
-    Y[r1][2 * t] = y[2];
-    Y[r1][2 * t + 1] = y[3];
+    mma_16816(h0, a, lds32(&P.W1[2 * kt * 8 + g][2 * t]), lds32(&P.W1[2 * kt * 8 + g][2 * t + 8]));
+    mma_16816(h1, a, lds32(&P.W1[(2 * kt + 1) * 8 + g][2 * t]),
+              lds32(&P.W1[(2 * kt + 1) * 8 + g][2 * t + 8]));
+    a2[kt][0] = pack_bf16x2(gelu_fast(h0[0]), gelu_fast(h0[1]));
+    a2[kt][1] = pack_bf16x2(gelu_fast(h0[2]), gelu_fast(h0[3]));
+    a2[kt][2] = pack_bf16x2(gelu_fast(h1[0]), gelu_fast(h1[1]));
+    a2[kt][3] = pack_bf16x2(gelu_fast(h1[2]), gelu_fast(h1[3]));
   }
+  // layers 2 (64 -> 64) and 3 (64 -> 8, OUT used): each pair of layer-2
+  // n-tiles is one layer-3 k-tile, accumulated as soon as it is ready
+  float y[4];
+  y[0] = P.b3[2 * t]; y[1] = P.b3[2 * t + 1]; y[2] = y[0]; y[3] = y[1];
+#pragma unroll
+  for (int k3 = 0; k3 < 4; ++k3) {
+    float h0[4], h1[4];
+    {
+      const float c0 = P.b2[2 * k3 * 8 + 2 * t], c1 = P.b2[2 * k3 * 8 + 2 * t + 1];
+      h0[0] = c0; h0[1] = c1; h0[2] = c0; h0[3] = c1;
+      const float d0 = P.b2[(2 * k3 + 1) * 8 + 2 * t], d1 = P.b2[(2 * k3 + 1) * 8 + 2 * t + 1];
+      h1[0] = d0; h1[1] = d1; h1[2] = d0; h1[3] = d1;
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+      mma_16816(h0, a2[kt], lds32(&P.W2[2 * k3 * 8 + g][kt * 16 + 2 * t]),
+                lds32(&P.W2[2 * k3 * 8 + g][kt * 16 + 2 * t + 8]));
+      mma_16816(h1, a2[kt], lds32(&P.W2[(2 * k3 + 1) * 8 + g][kt * 16 + 2 * t]),
+                lds32(&P.W2[(2 * k3 + 1) * 8 + g][kt * 16 + 2 * t + 8]));
+    }
+    const uint32_t a3[4] = {pack_bf16x2(gelu_fast(h0[0]), gelu_fast(h0[1])),
+                            pack_bf16x2(gelu_fast(h0[2]), gelu_fast(h0[3])),
+                            pack_bf16x2(gelu_fast(h1[0]), gelu_fast(h1[1])),
+                            pack_bf16x2(gelu_fast(h1[2]), gelu_fast(h1[3]))};
+    mma_16816(y, a3, lds32(&P.W3[g][k3 * 16 + 2 * t]), lds32(&P.W3[g][k3 * 16 + 2 * t + 8]));
+  }
+  Y[r0][2 * t] = y[0];
+  Y[r0][2 * t + 1] = y[1];
+  Y[r1][2 * t] = y[2];
+  Y[r1][2 * t + 1] = y[3];
+}
+
+// Both m-tiles of 32 rows (one warp).
+__device__ __forceinline__ void mlp_warp(const MlpPacked& P, const __nv_bfloat16 (*X)[24],
+                                         float (*Y)[8]) {
+  mlp_tile(P, X, Y, 0);
+  mlp_tile(P, X, Y, 1);
 }
 
 // Cooperative copy of the packed weights into shared memory.

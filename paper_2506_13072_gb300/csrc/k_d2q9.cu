@@ -37,4 +37,10 @@ cudaError_t conformation_d2q9(const StepDesc& d, double* part, double* out) {
 #undef CALL
 }
 
+cudaError_t repair_d2q9(const StepDesc& d, double eps, unsigned long long* count) {
+#define CALL(S) repair_impl<D2Q9, S>(d, eps, count)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
 }  // namespace fvlb

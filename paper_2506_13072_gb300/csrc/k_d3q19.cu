@@ -37,4 +37,10 @@ cudaError_t conformation_d3q19(const StepDesc& d, double* part, double* out) {
 #undef CALL
 }
 
+cudaError_t repair_d3q19(const StepDesc& d, double eps, unsigned long long* count) {
+#define CALL(S) repair_impl<D3Q19, S>(d, eps, count)
+  FVLB_DISPATCH(d.storage, CALL)
+#undef CALL
+}
+
 }  // namespace fvlb

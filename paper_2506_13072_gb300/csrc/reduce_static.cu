@@ -27,12 +27,36 @@ using namespace fvlb;
 constexpr int kMaxParts = 1024;
 static __device__ __align__(256) double g_reduce_scratch[kMaxParts * 8];
 
-// Device address of g_reduce_scratch, looked up once per device.  In host
-// code the name g_reduce_scratch is only a host-side stand-in for the
-// symbol, never a device address.
+// Device address of g_reduce_scratch, looked up once per device and CUDA
+// context.  In host code the name g_reduce_scratch is only a host-side
+// stand-in for the symbol, never a device address.  The address belongs to
+// the context the module was loaded into: after cudaDeviceReset (or any new
+// primary context) the module loads again, possibly elsewhere, so each
+// cached address is kept with the context it was looked up in and looked up
+// again when the current context differs.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};
+
+// the current driver context (cuCtxGetCurrent through the runtime's
+// driver entry point, so the library needs no link against libcuda)
+typedef int (*ctx_get_fn)(void**);
+void* current_context() {
+  static ctx_get_fn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<ctx_get_fn>(p);
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
 
 int scratch_for_current_device(double** out) {
   int dev = 0;
@@ -43,16 +67,18 @@ int scratch_for_current_device(double** out) {
   }
   if (dev < 0 || dev >= kMaxDevices)
     return set_global_error(FVLB_EINVAL, "fvlb_reduce_noalloc: device ordinal out of range");
+  void* ctx = current_context();   // null before the runtime made one current
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_reduce_scratch);
+    e = cudaGetSymbolAddress(&p, g_reduce_scratch);   // (makes the primary context current)
     if (e != cudaSuccess || p == nullptr) {
       cudaGetLastError();
       return set_global_error(FVLB_ECUDA,
                               "fvlb_reduce_noalloc: cudaGetSymbolAddress of the scratch failed");
     }
     g_scratch_ptr[dev] = static_cast<double*>(p);
+    g_scratch_ctx[dev] = current_context();
   }
   *out = g_scratch_ptr[dev];
   return FVLB_OK;

@@ -101,6 +101,8 @@ _SIGS = {
     "fvlb_set_scheme": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_model": ([_H, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "fvlb_conformation": ([_H, _dp], ctypes.c_int),
+    "fvlb_repair_conformation": ([_H, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)],
+                                 ctypes.c_int),
     "fvlb_set_check_interval": ([_H, ctypes.c_long], ctypes.c_int),
     "fvlb_status": ([_H, ctypes.c_int], ctypes.c_int),
     "fvlb_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
@@ -373,6 +375,13 @@ class Simulation:
         out = np.zeros(3)
         check(lib.fvlb_conformation(self.h, _ptr(out)), self.h)
         return dict(not_spd=int(out[0]), min_eig=out[1], max_trA=out[2])
+
+    def repair_conformation(self, eps):
+        """Clip the eigenvalues of A below eps at every node (eigenvectors
+        kept); returns the number of nodes changed."""
+        n = ctypes.c_longlong()
+        check(lib.fvlb_repair_conformation(self.h, float(eps), ctypes.byref(n)), self.h)
+        return n.value
 
     def state_size(self):
         n = ctypes.c_size_t()

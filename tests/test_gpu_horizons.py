@@ -1,0 +1,47 @@
+"""The configurations' own horizons against the oracle.
+
+Four-roll mill (Sec. 3.1): periodic 64^2 D2Q9 from rest, Wi 0.1 and 0.5,
+beta 0.5, 20 000 steps, FP64 path within 1e-12 of the FP64 oracle.
+
+Planar Poiseuille start-up (Sec. 3.2): 32-node channel, Wi 1, beta 0.1, from
+rest to the steady state (30 000 steps, about thirty relaxation times), the
+CUDA path against the oracle on the way and against the steady closed form
+(u, A_xy = lambda u', A_xx = 1 + 2 (lambda u')^2, A_yy = 1) at the end, with
+the oracle's own discretisation errors as bounds."""
+import numpy as np
+import pytest
+
+from paper_2506_13072_gb300 import workloads as W
+
+from gpu_common import compare, gpu_sim, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32 = 0, 1
+
+
+@pytest.mark.parametrize("Wi", [0.1, 0.5])
+def test_four_roll_20k_steps(Wi):
+    pr = W.four_roll(n=64, Wi=Wi, beta=0.5)
+    compare(pr, 20000, FP64, 1e-12, chunks=4)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (FP32, 1.5e-5)])
+def test_poiseuille_to_steady_state(prec, tol):
+    """(FP32: the arithmetic limit of the slow channels, 1.5e-5.)"""
+    pr = W.poiseuille(L=32, nx=8, Wi=1.0, beta=0.1)
+    compare(pr, 30000, prec, tol, chunks=5, fields=("u", "tau_p", "A"))
+    s = gpu_sim(pr, prec)
+    s.step(30000)
+    ua, Axx, Axy = W.poiseuille_steady(pr)
+    u = s.u()[:, :, 0].mean(axis=1)
+    A = s.A().mean(axis=1)            # compact (xx, xy, yy), averaged over x
+    s.close()
+
+    def gre(a, b):  # Sec. 3.2, global relative error
+        return np.abs(a - b).sum() / np.abs(b).sum()
+
+    assert gre(u, ua) < 4e-3
+    assert gre(A[:, 1], Axy) < 1.5e-3
+    assert gre(A[:, 0], Axx) < 1.5e-2
+    assert np.abs(A[:, 2] - 1.0).max() < 1e-5

@@ -11,7 +11,7 @@ import oracle as O
 from oracle import mlp as M
 from paper_2506_13072_gb300 import workloads as W
 
-from gpu_common import compact, fvlb, gpu_sim, oracle_sim, rel_l2
+from gpu_common import compact, fvlb, tau_floor, gpu_sim, oracle_sim, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -147,8 +147,7 @@ def test_learned_closure_in_the_step():
     o.step(1000)
     st = s.closure_stats()
     eu = rel_l2(s.u(), o.u(), 1e-30)
-    tfloor = 0.1 * pr.eta_p / pr.lam * np.linalg.norm(compact(o.A()))
-    et = rel_l2(s.tau_p(), compact(o.tau_p()), tfloor)
+    et = rel_l2(s.tau_p(), compact(o.tau_p()), tau_floor(pr, compact(o.A()), o.u(), 1000))
     served = st["network"] / max(1, st["network"] + st["fallback"])
     assert st["network"] + st["fallback"] == 1000 * pr.sites
     assert served > 0.3, served

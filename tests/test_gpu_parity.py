@@ -39,22 +39,35 @@ def test_four_roll_64_fp64(kernel, Wi):
     compare(pr, 300, FP64, TOL[FP64], kernel=kernel, chunks=3)
 
 
+# FP32 arithmetic limit.  An FP32 state resolves a population to 6e-8 of its
+# size; in the start-up of the slow, strongly stressed channels below each
+# step changes the velocity by 1e-3 of itself, so the rounding of 1000
+# coherent steps is bounded by 1000 x 3e-8 = 3e-5.  Measured (these cases,
+# 1000 steps): u 5.8e-6 / 7.3e-6, tau_p 1.00e-5 / 1.07e-5 (128-node
+# channel / Womersley), and 1.09e-5 for p of the 7 x 5 walled grid in the
+# split kernel.  A numpy emulation of the kernel's FP32 arithmetic gives the
+# same against an 80-bit reference (5.7e-6 / 1.1e-5 in the 128-node
+# channel), while FP32 storage with FP64 arithmetic gives 8e-8 / 2e-7, and
+# FP64 collisions with everything else FP32 still 4.5e-6 / 8.5e-6: the
+# rounding is spread over the velocity, its gradient and the stress source.
+# These three cases are held to 1.5e-5; every other FP32 case to 1e-5.
+FP32_LIMIT = 1.5e-5
+
+
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("L", [32, 128])
 def test_poiseuille_startup(prec, L):
-    """Planar Poiseuille start-up, walls on y, 8 periodic columns.  (In the
-    128-node channel both sides' FP64 rounding accumulates coherently to 1e-13
-    in A by step 1000, which tau_p = (eta_p/lambda)(A - I) amplifies; the
-    FP64 horizon here is 500 steps, longer runs are in test_long_run_drift.)"""
+    """Planar Poiseuille start-up, walls on y, 8 periodic columns, 1000 steps."""
     pr = W.poiseuille(L=L, nx=8, Wi=1.0, beta=0.1)
-    compare(pr, 500 if prec == FP64 else 1000, prec, TOL[prec], chunks=4,
-            fields=("u", "tau_p", "A"))
+    tol = FP32_LIMIT if (prec == FP32 and L == 128) else TOL[prec]
+    compare(pr, 1000, prec, tol, chunks=4, fields=("u", "tau_p", "A"))
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_womersley_cosine_force(prec):
     pr = W.womersley(L=64, nx=4, gamma=3.070, beta=0.5, Wi=0.5)
-    compare(pr, 1000, prec, TOL[prec], chunks=3, fields=("u", "tau_p", "A"))
+    tol = FP32_LIMIT if prec == FP32 else TOL[prec]
+    compare(pr, 1000, prec, tol, chunks=3, fields=("u", "tau_p", "A"))
 
 
 @pytest.mark.parametrize("name,prec,steps,bound", [
@@ -83,24 +96,42 @@ def test_ragged_d2q9(kernel, prec, shape, walls):
     pr = W.Problem("r", W.D2Q9, nx, ny, 1, 0.7, 0.15, 11.0, W.FORCE_CONST, (1e-5, -2e-5, 0.0),
                    walls=walls)
     _with_random(pr, seed=nx * 100 + ny)
-    compare(pr, 60, prec, TOL[prec], kernel=kernel, chunks=2)
+    tol = FP32_LIMIT if (prec == FP32 and kernel == 1 and shape == (7, 5)) else TOL[prec]
+    compare(pr, 60, prec, tol, kernel=kernel, chunks=2)
 
 
-# 16-bit storage.  Measured worst rel-L2 (u / tau_p) against the FP64 oracle
-# bound each case; the velocity target of 1e-3 is met by FP16 in these flows,
-# the stress target by FP16 with stochastic rounding only in the slower
-# channel, and by neither BF16 form.
+# 16-bit storage (flow populations as scaled deviations from the velocity
+# part of the receiving node's equilibrium, FP32 rest stress populations
+# carrying the rounding residuals).  Measured worst rel-L2 against the FP64
+# oracle (u / tau_p), over 1000 (four-roll) and 4000 (channel) steps:
+#   FP16 nearest      four-roll 2.3e-5 / 5.5e-4, Poiseuille 32 7.5e-4 / 8.3e-4,
+#                     Poiseuille 128 1.5e-5 / 5.4e-4, Womersley 4.2e-5 / 8.8e-4,
+#                     Womersley (gamma 5.3, Wi 2) 2.8e-5 / 7.1e-4
+#   FP16 stochastic   the same within 1e-3 except tau_p in the channels
+#                     (2.8e-3 Poiseuille 32, 1.25e-3 Womersley)
+#   BF16 (both)       u 2e-4 .. 6e-3, tau_p 4e-3 .. 1.3e-2
+# FP16 with nearest rounding is the form that meets 1e-3 in every flow; the
+# bounds below are 1e-3 for it and the measured errors (rounded up) for the
+# others.
 FP16SR, BF16SR = 4, 5
 REDUCED = {
     # (form, flow): (steps, u bound, tau_p bound)
-    (FP16, "four_roll"): (1000, 1e-3, 2e-3),
-    (BF16, "four_roll"): (1000, 6e-3, 1.5e-2),
-    (FP16SR, "four_roll"): (1000, 1e-3, 2e-3),
-    (BF16SR, "four_roll"): (1000, 6e-3, 1.5e-2),
-    (FP16, "poiseuille128"): (1000, 1e-2, 1e-2),
-    (FP16SR, "poiseuille128"): (4000, 1e-3, 3e-3),
-    (BF16SR, "poiseuille128"): (4000, 8e-3, 2.5e-2),
-    (FP16SR, "womersley64"): (4000, 5e-3, 6e-3),
+    (FP16, "four_roll"): (1000, 1e-3, 1e-3),
+    (FP16, "poiseuille32"): (4000, 1e-3, 1e-3),
+    (FP16, "poiseuille128"): (4000, 1e-3, 1e-3),
+    (FP16, "womersley64"): (4000, 1e-3, 1e-3),
+    (FP16, "womersley64_wi2"): (4000, 1e-3, 1e-3),
+    (FP16SR, "four_roll"): (1000, 1e-3, 1e-3),
+    (FP16SR, "poiseuille128"): (4000, 1e-3, 1e-3),
+    (FP16SR, "poiseuille32"): (4000, 1.2e-3, 3.5e-3),
+    (FP16SR, "womersley64"): (4000, 1e-3, 1.6e-3),
+    (BF16, "four_roll"): (1000, 5e-4, 6e-3),
+    (BF16, "poiseuille32"): (4000, 8e-3, 7e-3),
+    (BF16, "poiseuille128"): (4000, 2e-4, 6e-3),
+    (BF16, "womersley64"): (4000, 1.5e-3, 9e-3),
+    (BF16SR, "four_roll"): (1000, 5e-4, 8e-3),
+    (BF16SR, "poiseuille128"): (4000, 2e-4, 9e-3),
+    (BF16SR, "womersley64"): (4000, 1.2e-3, 1.3e-2),
 }
 
 
@@ -109,8 +140,12 @@ def test_reduced_precision(prec, flow):
     steps, bu, bt = REDUCED[(prec, flow)]
     if flow == "four_roll":
         pr = W.four_roll(n=64, Wi=0.5, beta=0.5)
+    elif flow == "poiseuille32":
+        pr = W.poiseuille(L=32, nx=8, Wi=1.0, beta=0.1)
     elif flow == "poiseuille128":
         pr = W.poiseuille(L=128, nx=8, Wi=1.0, beta=0.1)
+    elif flow == "womersley64_wi2":
+        pr = W.womersley(L=64, nx=4, gamma=5.317, beta=0.5, Wi=2.0)
     else:
         pr = W.womersley(L=64, nx=4, gamma=3.070, beta=0.5, Wi=0.5)
     w = compare(pr, steps, prec, 1.0, chunks=4, fields=("u", "tau_p"))
@@ -140,8 +175,8 @@ def test_ragged_d3q19(kernel, prec, shape, walls):
     compare(pr, 20, prec, TOL[prec], kernel=kernel, chunks=2)
 
 
-@pytest.mark.parametrize("prec,bu,bt", [(FP16, 1e-3, 2e-3), (FP16SR, 2e-3, 2e-3),
-                                         (BF16, 8e-3, 1.5e-2), (BF16SR, 1.5e-2, 1.5e-2)])
+@pytest.mark.parametrize("prec,bu,bt", [(FP16, 1e-3, 1e-3), (FP16SR, 1e-3, 1e-3),
+                                         (BF16, 1.5e-3, 4e-3), (BF16SR, 2e-3, 5e-3)])
 def test_reduced_precision_taylor_green(prec, bu, bt):
     pr = W.taylor_green_3d(n=32, U0=0.02, Re=100, Wi=1.0, beta=0.5)
     w = compare(pr, 200, prec, 1.0, chunks=2, fields=("u", "tau_p"))
@@ -155,12 +190,13 @@ def test_reduced_precision_taylor_green(prec, bu, bt):
 # tile's ragged tail leaves part of a warp without nodes); with nx odd it
 # loads them directly.  An exchanged or misplaced chunk or half of a pair
 # gives errors of order one; the bounds are those of the 16-bit forms above
-# for a short horizon.
+# (FP16 1e-3; BF16 with stochastic rounding, measured 1.1e-2 / 7e-3 on
+# these random states).
 RAGGED16 = [((34, 5, 6), 0b001), ((37, 4, 5), 0b010), ((66, 3, 4), 0), ((40, 5, 4), 0b100),
             ((66, 9), 0b01), ((33, 17), 0b10), ((130, 5), 0), ((136, 9), 0b01)]
 
 
-@pytest.mark.parametrize("prec,bu,bt", [(FP16, 2e-3, 4e-3), (BF16SR, 1.5e-2, 3e-2)])
+@pytest.mark.parametrize("prec,bu,bt", [(FP16, 1e-3, 1e-3), (BF16SR, 1.5e-2, 1.5e-2)])
 @pytest.mark.parametrize("shape,walls", RAGGED16)
 def test_ragged_16bit(prec, bu, bt, shape, walls):
     if len(shape) == 3:
@@ -220,7 +256,7 @@ def test_full_size_d2q9_2048(prec):
     """2048^2 D2Q9, the grid and launch shape of the benchmark's D2Q9 forms."""
     small = W.four_roll(n=32, Wi=0.5, beta=0.5)
     _with_random(small, seed=6)
-    _tiled_check(small, 64, 12, prec, TOL[prec] if prec == FP32 else 2e-3)
+    _tiled_check(small, 64, 12, prec, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", [FP16, BF16])
@@ -229,7 +265,7 @@ def test_full_size_d3q19_256_16bit(prec):
     bounds of the 16-bit Taylor-Green forms (u and tau_p together)."""
     small = W.Problem("t", W.D3Q19, 16, 16, 16, 0.52, 0.004, 800.0)
     _with_random(small, seed=5, U=0.02, dA=0.3)
-    _tiled_check(small, 16, 6, prec, 2e-3 if prec == FP16 else 1.5e-2)
+    _tiled_check(small, 16, 6, prec, 1e-3 if prec == FP16 else 5e-3)
 
 
 # ---------------------------------------------------------------------------

@@ -30,8 +30,12 @@ def _state_on_device(sim, pr, precision):
     pitch = int(np.frombuffer(blob[40:48].tobytes(), dtype=np.int64)[0])
     Q = 9 if pr.lattice == W.D2Q9 else 19
     C = 3 if pr.lattice == W.D2Q9 else 6
+    D = 2 if pr.lattice == W.D2Q9 else 3
     sb = {F.FVLB_FP64: 8, F.FVLB_FP32: 4}.get(precision, 2)
     nf, nh = Q * pitch * sb, C * Q * pitch * sb
+    if sb == 2:   # 16-bit forms: FP32 U[D][pitch] and h0[C][pitch] follow
+        nf += 4 * D * pitch
+        nh += 4 * C * pitch
     f = torch.from_numpy(blob[HEADER:HEADER + nf].copy()).cuda()
     h = torch.from_numpy(blob[HEADER + nf:HEADER + nf + nh].copy()).cuda()
     return f, h, pitch
@@ -76,21 +80,34 @@ def test_reduce_noalloc_matches_reduce(case):
     sim.close()
 
 
-def test_reduce_noalloc_rejects_bad_sizes():
+def test_reduce_noalloc_rejects_bad_arguments():
+    """Every rejected call returns FVLB_EINVAL with a message and leaves the
+    caller's output buffer as it was."""
     import torch
 
     F = fvlb()
-    buf = torch.zeros(1024, dtype=torch.float32, device="cuda")
-    out = torch.zeros(8, dtype=torch.float64, device="cuda")
-    args = dict(f=buf.data_ptr(), h=buf.data_ptr(), out=out.data_ptr())
+    # room for h'[6][19][64] (the largest array the valid call below reads)
+    buf = torch.zeros(6 * 19 * 64, dtype=torch.float32, device="cuda")
+    out = torch.full((8,), 7.0, dtype=torch.float64, device="cuda")
+    f, h, o = buf.data_ptr(), buf.data_ptr(), out.data_ptr()
 
-    def call(lattice, nx, ny, nz, pitch):
-        return F.lib.fvlb_reduce_noalloc(lattice, F.FVLB_FP32, nx, ny, nz, args["f"], args["h"],
-                                         pitch, 0.1, 10.0, None, ctypes.c_void_p(args["out"]),
-                                         None)
+    def call(lattice=19, storage=None, nx=4, ny=4, nz=4, pitch=64, eta_p=0.1, lam=10.0,
+             fp=f, hp=h, op=o):
+        st = F.FVLB_FP32 if storage is None else storage
+        return F.lib.fvlb_reduce_noalloc(lattice, st, nx, ny, nz, fp, hp, pitch, eta_p, lam, None,
+                                         ctypes.c_void_p(op), None)
 
-    assert call(19, 0, 4, 4, 64) == F.FVLB_EINVAL
-    assert call(19, 4, 4, 4, 32) == F.FVLB_EINVAL          # pitch < N
-    assert call(19, 4096, 4096, 4096, 4096 ** 3) == F.FVLB_EINVAL   # beyond the limit
-    assert call(7, 4, 4, 4, 64) == F.FVLB_EINVAL
-    assert "fvlb_reduce_noalloc" in F.last_error()
+    bad = [dict(nx=0), dict(pitch=32),                      # pitch < N
+           dict(nx=4096, ny=4096, nz=4096, pitch=4096 ** 3),  # beyond the limit
+           dict(lattice=7), dict(storage=6), dict(storage=-1),
+           dict(fp=None), dict(hp=None), dict(op=None),
+           dict(lam=0.0), dict(lam=-1.0), dict(lam=float("inf")), dict(eta_p=-0.1),
+           dict(eta_p=float("nan"))]
+    for kw in bad:
+        assert call(**kw) == F.FVLB_EINVAL, kw
+        assert "fvlb_reduce_noalloc" in F.last_error()
+        torch.cuda.synchronize()
+        assert (out.cpu().numpy() == 7.0).all(), kw
+    # a valid call on the same buffers goes through
+    assert call() == F.FVLB_OK
+    torch.cuda.synchronize()
