@@ -11,7 +11,7 @@ import oracle as O
 from oracle import mlp as M
 from paper_2506_13072_gb300 import workloads as W
 
-from gpu_common import compact, fvlb, tau_floor, gpu_sim, oracle_sim, rel_l2
+from gpu_common import compact, fvlb, tau_floor, gpu_sim, oracle_sim, rel_l2, tiled_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -129,7 +129,99 @@ def _train_2d(F, seed=0):
     return net, loss
 
 
-def test_learned_closure_in_the_step():
+@pytest.fixture(scope="module")
+def net2d():
+    F = fvlb()
+    net, loss = _train_2d(F)
+    yield net, loss
+    net.close()
+
+
+def _train_3d(F, seed=0):
+    """The 3D network as the benchmark trains it: pairs from Taylor-Green
+    32^3 runs of the plain method (Wi 1 and 0.2), relative loss."""
+    net = F.Mlp(W.D3Q19, capacity=1 << 20, seed=seed)
+    for Wi in (1.0, 0.2):
+        small = W.taylor_green_3d(n=32, U0=0.02, Re=100, Wi=Wi, beta=0.5)
+        s = gpu_sim(small, F.FVLB_FP32)
+        for _ in range(8):
+            s.step(100)
+            net.collect(s, stride=5)
+        s.close()
+    net.set_loss(1e-3)
+    for steps, batch, lr in ((10000, 1024, 2e-3), (10000, 2048, 5e-4), (10000, 4096, 1e-4)):
+        net.train(steps, batch=batch, lr=lr)
+    return net
+
+
+@pytest.fixture(scope="module")
+def net3d():
+    F = fvlb()
+    net = _train_3d(F)
+    yield net
+    net.close()
+
+
+def _closure_run(pr, net, steps, tol=1e-2):
+    F = fvlb()
+    s = gpu_sim(pr, F.FVLB_FP32)
+    s.set_closure(net, tol=tol)
+    s.step(steps)
+    st = s.closure_stats()
+    served = st["network"] / max(1, st["network"] + st["fallback"])
+    assert st["network"] + st["fallback"] == steps * pr.sites
+    return s, served
+
+
+def test_learned_closure_taylor_green_3d(net3d):
+    """D3Q19 Taylor-Green 32^3, Wi 1 (the 3D network's own flow), 300 steps
+    with the closure against the FP64 oracle's plain method: within 1e-3 in
+    u and tau_p, with the fraction of node updates the network served."""
+    pr = W.taylor_green_3d(n=32, U0=0.02, Re=100, Wi=1.0, beta=0.5)
+    s, served = _closure_run(pr, net3d, 300)
+    o = oracle_sim(pr)
+    o.step(300)
+    eu = rel_l2(s.u(), o.u(), 1e-30)
+    et = rel_l2(s.tau_p(), compact(o.tau_p()), tau_floor(pr, compact(o.A()), o.u(), 300))
+    s.close()
+    print(f"3D closure, TGV 32^3: served {served:.4f}, rel-L2 u {eu:.2e} tau_p {et:.2e}")
+    assert eu < 1e-3 and et < 1e-3, (eu, et, served)
+
+
+def test_learned_closure_taylor_green_256_tiled(net3d):
+    """The benchmark's closure launch shape, 256^3: the Taylor-Green field of
+    a 32^3 box repeated 8 times per axis evolves as the 32^3 solution tiled,
+    so the oracle on 32^3 gives every node (closure and fallback nodes
+    alike are node-local)."""
+    small = W.taylor_green_3d(n=32, U0=0.02, Re=100, Wi=1.0, beta=0.5)
+    small.A0 = np.broadcast_to(np.eye(3), small.shape + (3, 3)).copy()
+    big = tiled_problem(small, 8)
+    s, served = _closure_run(big, net3d, 20)
+    o = oracle_sim(small)
+    o.step(20)
+    eu = rel_l2(s.u(), np.tile(o.u(), (8, 8, 8, 1)), 1e-30)
+    et = rel_l2(s.tau_p(), np.tile(compact(o.tau_p()), (8, 8, 8, 1)), 1e-30)
+    s.close()
+    assert eu < 1e-3 and et < 1e-3, (eu, et, served)
+
+
+def test_learned_closure_four_roll_1024(net2d):
+    """D2Q9 four-roll mill 1024^2 (k = 2 pi / 1024, the config's closure
+    grid), from the forced velocity field, 40 steps with the closure against
+    the FP64 oracle's plain method on the full grid."""
+    net, _ = net2d
+    pr = W.four_roll(n=1024, Wi=0.5, beta=0.5, at_rest=False)
+    s, served = _closure_run(pr, net, 40)
+    o = oracle_sim(pr)
+    o.step(40)
+    eu = rel_l2(s.u(), o.u(), 1e-30)
+    et = rel_l2(s.tau_p(), compact(o.tau_p()), tau_floor(pr, compact(o.A()), o.u(), 40))
+    s.close()
+    print(f"2D closure, four-roll 1024^2: served {served:.4f}, rel-L2 u {eu:.2e} tau_p {et:.2e}")
+    assert eu < 1e-3 and et < 1e-3, (eu, et, served)
+
+
+def test_learned_closure_in_the_step(net2d):
     """Trained on pairs from the plain method (four-roll, Poiseuille,
     Womersley trajectories), the network stands in for chi in a four-roll
     run; nodes whose network chi is off by more than 1e-2 relative use the
@@ -137,7 +229,7 @@ def test_learned_closure_in_the_step():
     reports what the network gains: the fraction of nodes it serves and the
     throughput ratio against the analytic step."""
     F = fvlb()
-    net, loss = _train_2d(F)
+    net, loss = net2d
     assert loss < 3e-2, loss          # relative mean squared error of the last minibatch
     pr = W.four_roll(n=64, Wi=0.5, beta=0.5)
     s = gpu_sim(pr, F.FVLB_FP32)
@@ -169,4 +261,3 @@ def test_learned_closure_in_the_step():
     print(f"learned closure: served {served:.3f} of node updates, rel-L2 u {eu:.2e} "
           f"tau_p {et:.2e}, MLUPS {rates[True]:.0f} vs analytic {rates[False]:.0f}")
     s.close()
-    net.close()
