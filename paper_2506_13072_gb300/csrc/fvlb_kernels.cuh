@@ -431,9 +431,9 @@ struct NoClosureSmem {
 //    (otherwise a second barrier closes each plane).  Node-major, each
 //    node's C values padded to CP for vector loads.
 // The budget is the 48 KB of static shared memory for one node per thread;
-// with more, the tile lives in dynamic shared memory sized for two blocks
-// per SM.
-template <class L, class S, int GX, int TY, bool FW, bool CL, int XN>
+// with more, the tile lives in dynamic shared memory sized for MINB blocks
+// per SM (two: 110 KB; three: 72 KB).
+template <class L, class S, int GX, int TY, bool FW, bool CL, int XN, int MINB = 2>
 struct TileCfg {
   using R = RT<S>;
   using X = typename Store<S>::X;
@@ -458,7 +458,7 @@ struct TileCfg {
   // (whose stage fills the static 48 KB and leaves no room for the
   // double-buffered exchange or a third stage)
   static constexpr bool kDynamic = XN > 1 || (PF && D == 2);
-  static constexpr size_t kLimit = kDynamic ? 110 * 1024 : 48 * 1024;
+  static constexpr size_t kLimit = kDynamic ? (MINB >= 3 ? 72 : 110) * 1024 : 48 * 1024;
   static constexpr int NST =
       (PF && kRing + sizeof(CLS) + 3 * kStage1 + 2 * kEx1 <= kLimit) ? 3 : 2;
   static constexpr int NBUF = (kRing + sizeof(CLS) + NST * kStage1 + 2 * kEx1 <= kLimit) ? 2 : 1;
@@ -481,14 +481,14 @@ struct TileCfg {
 // march axis.  Called by k_step_fused (one tile per block) and by the
 // batched persistent kernel (many tiles of many grids per block).
 template <class L, class S, int GX, int TY, bool WALLS, bool FW, bool CL = false, int XN = 1,
-          bool ORIG = false>
+          bool ORIG = false, int MINB = 2>
 __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                                            const Bufs<S>& b, int mchunk, int bx, int by,
                                            int bz) {
   using R = RT<S>;
   using X = typename Store<S>::X;
   using Sh = FusedShape<L, GX, TY, FW, XN>;
-  using Cfg = TileCfg<L, S, GX, TY, FW, CL, XN>;
+  using Cfg = TileCfg<L, S, GX, TY, FW, CL, XN, MINB>;
   constexpr int D = L::D, Q = L::Q, C = L::C;
   constexpr int NCW = Sh::NCW, TXS = Sh::TXS, EX = Sh::EX, NE = Sh::NE;
   constexpr int NFW = Sh::NFW, SPF = Sh::SPF;
@@ -1298,7 +1298,7 @@ template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool 
           int XN = 1, bool ORIG = false>
 __global__ void __launch_bounds__(FusedShape<L, GX, TY, FW, XN>::NT, MINB)
     k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
-  fused_tile<L, S, GX, TY, WALLS, FW, CL, XN, ORIG>(g, ph, b, mchunk, blockIdx.x, blockIdx.y,
+  fused_tile<L, S, GX, TY, WALLS, FW, CL, XN, ORIG, MINB>(g, ph, b, mchunk, blockIdx.x, blockIdx.y,
                                                     blockIdx.z);
 }
 

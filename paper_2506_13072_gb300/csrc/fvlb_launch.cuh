@@ -90,7 +90,7 @@ template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool 
 cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                           const Bufs<S>& b, int mchunk) {
   constexpr int NT = FusedShape<L, GX, TY, FW, XN>::NT;
-  constexpr size_t dyn = TileCfg<L, S, GX, TY, FW, CL, XN>::kDynamicBytes;
+  constexpr size_t dyn = TileCfg<L, S, GX, TY, FW, CL, XN, MINB>::kDynamicBytes;
   auto kern = k_step_fused<L, S, GX, TY, MINB, WALLS, FW, CL, XN, ORIG>;
   if constexpr (dyn > 0) {
     const cudaError_t e = allow_dynamic_smem(kern, dyn);
@@ -149,8 +149,16 @@ cudaError_t fused_step(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
       if constexpr (!ORIG) {
         if (d.mlp) return launch_fused<L, S, 1, 1, 2, true, 1>(d, g, ph, b);
       }
+      // three blocks per SM (64 registers, two copy stages) on request, for
+      // measurement against the default two
+      if (tune_int("FVLB_FP32_3D_BLOCKS", 2) == 3)
+        return launch_fused<L, S, 1, 1, 3, true, 2, ORIG>(d, g, ph, b);
       return launch_fused<L, S, 1, 1, 2, true, 2, ORIG>(d, g, ph, b);
     } else {
+      if constexpr (!ORIG) {   // 16-bit: the same choice (present scheme)
+        if (tune_int("FVLB_16_3D_BLOCKS", 2) == 3)
+          return launch_fused<L, S, 1, 1, 3, true, 1>(d, g, ph, b);
+      }
       return launch_fused<L, S, 1, 1, 2, true, 1, ORIG>(d, g, ph, b);
     }
   }
