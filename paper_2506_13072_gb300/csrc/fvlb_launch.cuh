@@ -149,16 +149,8 @@ cudaError_t fused_step(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
       if constexpr (!ORIG) {
         if (d.mlp) return launch_fused<L, S, 1, 1, 2, true, 1>(d, g, ph, b);
       }
-      // three blocks per SM (64 registers, two copy stages) on request, for
-      // measurement against the default two
-      if (tune_int("FVLB_FP32_3D_BLOCKS", 2) == 3)
-        return launch_fused<L, S, 1, 1, 3, true, 2, ORIG>(d, g, ph, b);
       return launch_fused<L, S, 1, 1, 2, true, 2, ORIG>(d, g, ph, b);
     } else {
-      if constexpr (!ORIG) {   // 16-bit: the same choice (present scheme)
-        if (tune_int("FVLB_16_3D_BLOCKS", 2) == 3)
-          return launch_fused<L, S, 1, 1, 3, true, 1>(d, g, ph, b);
-      }
       return launch_fused<L, S, 1, 1, 2, true, 1, ORIG>(d, g, ph, b);
     }
   }
