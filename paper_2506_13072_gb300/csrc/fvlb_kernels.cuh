@@ -139,7 +139,8 @@ __device__ __forceinline__ long long push_dest(const Grid& g, int i, int x, int 
 
 // p = c_s^2 / (1 - w_0) [sum_{i!=0} f_i + s_0(u) + tau_f F_0 + tau_f f^B_0]
 // (Sec. 2.2, Appendix B) with F_0 = -3 w_0 (1 - 1/(2 tau_f)) F.u and
-// s_0 = -1.5 w_0 |u|^2.
+// s_0 = -1.5 w_0 |u|^2; returned as the pressure variable of p_part (p in
+// FP64, p / (3 w_1) in FP32).
 template <class L, class R>
 __device__ __forceinline__ R pressure(const Phys<R>& ph, const R (&f)[L::Q],
                                       const R (&u)[L::D], const R F[3], R fB0) {
@@ -155,7 +156,7 @@ __device__ __forceinline__ R pressure(const Phys<R>& ph, const R (&f)[L::Q],
   constexpr double w0 = L::w(0);
   const R s0 = R(-1.5 * w0) * uu;
   const R F0 = R(-3.0 * w0) * ph.kf * Fu;
-  return R(1.0 / (3.0 * (1.0 - w0))) * (sum + s0 + ph.tau_f * F0 + ph.tau_f * fB0);
+  return p_part<L, R>(sum + s0 + ph.tau_f * F0 + ph.tau_f * fB0);
 }
 
 // ---------------------------------------------------------------------------
@@ -238,7 +239,17 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
   // 16-bit forms: the rest stress populations (stored last, in FP32, with
   // the rounding residuals of the component's other populations) and this
   // node's velocity for the flow populations it receives next step
-  R h0post[Store<S>::V2 ? C : 1], hres[Store<S>::V2 ? C : 1];
+  // The rest stress population keeps the node's populations summing to the
+  // post-collision zeroth moment (as in the fused step): FP32 storage takes
+  // it as that moment minus the other populations' sum; the 16-bit forms
+  // take the rounding residuals less the rounded weights' excess
+  constexpr bool RS = std::is_same<S, float>::value;
+  constexpr double kWx = weight_sum_excess<L, R>();
+  R h0post[Store<S>::V2 ? C : 1], hres[(Store<S>::V2 || RS) ? C : 1];
+  if constexpr (RS) {
+#pragma unroll
+    for (int k = 0; k < C; ++k) hres[k] = R(0);
+  }
   if constexpr (Store<S>::V2) {
 #pragma unroll
     for (int k = 0; k < C; ++k) hres[k] = R(0);
@@ -261,9 +272,10 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
     const R wi = R(L::w(i));
 
     // flow: f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
-    const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
-    const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-    const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
+    const R lam_i = R(p_coef<L, R>(i));
+    const R w3i = R(w3<L, R>(i));
+    const R feq = lam_i * p + (w3i * cu + wi * (R(4.5) * cu * cu - R(1.5) * uu));
+    const R Fi = ph.kf * (w3i * cF + wi * (R(9) * cF * cu - R(3) * Fu));
     const R fBi = ORIG ? R(0) : fB_dir<L, R>(i, Ad, kB);
     const R fpost = f[i] - (f[i] - feq) * ph.inv_tau_f + fBi + Fi;
     if constexpr (Store<S>::V2) {
@@ -290,15 +302,25 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
       const R post = hi - (hi - heq) * ph.inv_tau_h + phi * src[k];
       if constexpr (Store<S>::V2) {
         if (i == 0) {
-          h0post[k] = post;
+          // less the weights' excess times the weight-proportional part
+          h0post[k] = post - R(kWx) * (ph.inv_tau_h * Ad[k] + src[k]);
         } else {
           S* q = b.h_out + (long long)(k * Q + j) * P + d;
           hres[k] += post - Store<S>::st_r(q, post, Store<S>::sr ? lcg_next(rng) : 0u);
+        }
+      } else if constexpr (RS) {
+        if (i != 0) {
+          hres[k] += post;
+          store_h<L, S>(b.h_out, P, d, k, j, post, 0u);
         }
       } else {
         store_h<L, S>(b.h_out, P, d, k, j, post, Store<S>::sr ? lcg_next(rng) : 0u);
       }
     }
+  }
+  if constexpr (RS) {
+#pragma unroll
+    for (int k = 0; k < C; ++k) store_h<L, S>(b.h_out, P, s, k, 0, (Ad[k] + src[k]) - hres[k], 0u);
   }
   if constexpr (Store<S>::V2) {
     float* h0o = h_ext<L>(b.h_out, P);
@@ -565,6 +587,9 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   // u = U + sum_i c_i s_i / KF + F/2 (the velocity part e_i(U) of the
   // stored deviations carries momentum U and no other first moment).
   constexpr bool V2 = Cfg::V2;
+  // FP32 storage: the rest stress population from the post-collision zeroth
+  // moment (see the collision)
+  constexpr bool RS = std::is_same<S, float>::value;
   constexpr int FQ = V2 ? Q + D : Q;
   auto fill_store = [&](int e, bool ok, int mm, int gx, int gy, const R (&fv)[FQ], int q) {
     R u[D];
@@ -594,6 +619,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     Vel<R, D> t;
 #pragma unroll
     for (int a = 0; a < (D == 3 ? 4 : 2); ++a) t.v[a] = a < D ? u[a] : R(0);
+    if constexpr (D == 3) t.v[3] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];  // |u|^2
     ring[slot(q)][e] = t;
   };
   auto fill_load = [&](bool ok, int mm, int gx, int gy, R (&fv)[FQ]) {
@@ -1029,8 +1055,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       // 16-bit forms: the node's stored velocity U (the reference of its
       // flow populations), and the sum of e_i(U) over i != 0
       R Us[V2 ? D : 1];
+      R UU = R(0);
       if constexpr (V2) {
-        R UU = R(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           Us[a] = stage_e[st][1 + a][col];
@@ -1054,9 +1080,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       // pressure (Sec. 2.2, Appendix B)
       constexpr double w0 = L::w(0);
       const R fB0 = fB_dir<L, R>(0, Ad, kB);
-      const R p = R(1.0 / (3.0 * (1.0 - w0))) *
-                  (sumf + R(-1.5 * w0) * uu + ph.tau_f * (R(-3.0 * w0) * ph.kf * Fu) +
-                   ph.tau_f * fB0);
+      const R p = p_part<L, R>(sumf + R(-1.5 * w0) * uu +
+                               ph.tau_f * (R(-3.0 * w0) * ph.kf * Fu) + ph.tau_f * fB0);
 
       // Work that depends on the stress component k is dispatched once on
       // k (warp-uniform), so that every population index and coefficient
@@ -1179,18 +1204,16 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       // velocity of the node that receives population i: the ring holds the
       // tile's neighbours (periodic images included); through a wall the
       // population comes back to this node
-      auto dest_u = [&](int i, bool bounced, R (&ud)[D]) {
-        if (bounced) {
-#pragma unroll
-          for (int a = 0; a < D; ++a) ud[a] = u[a];
-          return;
-        }
+      // (and its |u|^2: the 3D ring record carries it in its fourth slot)
+      auto dest_u = [&](int i, bool bounced, R (&ud)[D]) -> R {
         const int cm = D == 3 ? L::cz(i) : L::cy(i);
-        const int rs = cm == 1 ? rp : (cm == -1 ? rm : rc);
-        const int es = eo + L::cx(i) + (D == 3 ? L::cy(i) * EX : 0);
+        const int rs = bounced ? rc : (cm == 1 ? rp : (cm == -1 ? rm : rc));
+        const int es = bounced ? eo : eo + L::cx(i) + (D == 3 ? L::cy(i) * EX : 0);
         const Vel<R, D> t = ring[rs][es];
 #pragma unroll
         for (int a = 0; a < D; ++a) ud[a] = t.v[a];
+        if constexpr (D == 3) return t.v[3];
+        else return ud[0] * ud[0] + ud[1] * ud[1];
       };
       auto emit = [&](auto FASTC) {
         constexpr bool FAST = decltype(FASTC)::value;
@@ -1209,7 +1232,16 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
             return (uint32_t)j * P32 + d;
           }
         };
-        R h0post = R(0), hres = R(0);   // 16-bit forms: rest population, residuals
+        // The rest population (i = 0, which stays at this node) keeps the
+        // node's stored populations summing to the post-collision zeroth
+        // moment (A - I)_k + src (sum_i w_i = 1, sum_i w_i c_i = 0):
+        //  - FP32: it is that moment minus the other populations' sum, so
+        //    neither the rounded weights (whose sum exceeds one by 7e-9 in
+        //    2D, 1.5e-8 in 3D) nor the rounding of the collision moves A;
+        //  - 16-bit forms: it takes the rounding residuals of the 16-bit
+        //    stores, less the weights' excess times alpha.
+        constexpr double kWx = weight_sum_excess<L, R>();
+        R h0post = R(0), hres = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           R cu = R(0);
@@ -1227,14 +1259,20 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
             hvi = hv[i];
           }
           const R wa = R(L::w(i)) * alpha, wb = R(L::w(i)) * beta;
-          const R post = keep * hvi + (wa + cu * wb);
+          R post = keep * hvi + (wa + cu * wb);
           if constexpr (V2) {
             if (i == 0) {
-              h0post = post;
+              h0post = post - R(kWx) * alpha;
             } else {
               bool bnc;
               const uint32_t o = index(i, bnc);
               hres += post - Store<S>::st_r(hout_k + o, post, Store<S>::sr ? lcg_next(rng) : 0u);
+            }
+          } else if constexpr (RS) {
+            if (i != 0) {
+              hres += post;
+              bool bnc;
+              Store<S>::st(hout_k + index(i, bnc), post, 0u);
             }
           } else {
             bool bnc;
@@ -1242,6 +1280,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           }
         }
         if constexpr (V2) h_ext<L>(b.h_out, P)[(uint32_t)k * P32 + sn32] = float(h0post + hres);
+        if constexpr (RS) Store<S>::st(hout_k + sn32, (Ad_k + src) - hres, 0u);
 
         // f_i, i = k (mod C): f* = f - (f - f^eq)/tau_f + f^B + F_i (Sec. 2.2)
         on_component(k, [&](auto KC) {
@@ -1259,22 +1298,23 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                 if (c == -1) { cu -= u[a]; cF -= F[a]; }
               }
               const R wi = R(L::w(i));
-              const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
-              const R feq = lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-              const R Fi = wi * ph.kf * (R(3) * cF + R(9) * cF * cu - R(3) * Fu);
+              const R lam_i = R(p_coef<L, R>(i));
+              const R w3i = R(w3<L, R>(i));
+              const R feq = lam_i * p + (w3i * cu + wi * (R(4.5) * cu * cu - R(1.5) * uu));
+              const R Fi = ph.kf * (w3i * cF + wi * (R(9) * cF * cu - R(3) * Fu));
               const R fBi = fB_dir<L, R>(i, Ad, kB);
               R foi;
               if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][col]);
               else foi = fo[jj];
-              if constexpr (V2) foi = foi * R(1.0f / Store<S>::KF) + feq_u<L, R>(i, Us);
+              if constexpr (V2) foi = foi * R(1.0f / Store<S>::KF) + feq_u<L, R>(i, Us, UU);
               const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
               bool bnc;
               const uint32_t o = index(i, bnc);
               if constexpr (V2) {
                 // scaled deviation from e_j(u) of the receiving node
                 R ud[D];
-                dest_u(i, bnc, ud);
-                const R ej = feq_u<L, R>(bnc ? L::opp(i) : i, ud);
+                const R uud = dest_u(i, bnc, ud);
+                const R ej = feq_u<L, R>(bnc ? L::opp(i) : i, ud, uud);
                 Store<S>::st(b.f_out + o, R(Store<S>::KF) * (post - ej),
                              Store<S>::sr ? lcg_next(rng) : 0u);
               } else {
@@ -1536,7 +1576,7 @@ __global__ void k_init(Grid g, S* __restrict__ f, S* __restrict__ h,
 #pragma unroll
     for (int k = 0; k < C; ++k)
       A[k] = A0 ? R(A0[s * C + k]) : (L::ca(k) == L::cb(k) ? R(1) : R(0));
-    const R p = p0 ? R(p0[s]) : R(0);
+    const R p = p_part_of_p<L, R>(p0 ? R(p0[s]) : R(0));
     R hres[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) hres[k] = R(0);
@@ -1546,12 +1586,13 @@ __global__ void k_init(Grid g, S* __restrict__ f, S* __restrict__ h,
 #pragma unroll
       for (int a = 0; a < D; ++a) cu += R(cc<L>(i, a)) * u[a];
       const R wi = R(L::w(i));
-      const R lam_i = i == 0 ? R((L::w(0) - 1.0) * 3.0) : R(L::w(i) * 3.0);
+      const R lam_i = R(p_coef<L, R>(i));
       if constexpr (Store<S>::V2) {
         // f^eq(p, u) - e_i(u) = lam_i p, scaled; U = u
         Store<S>::st(f + i * P + s, R(Store<S>::KF) * (lam_i * p), 0x80000000u);
       } else {
-        Store<S>::st(f + i * P + s, lam_i * p + wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu),
+        Store<S>::st(f + i * P + s,
+                     lam_i * p + (R(w3<L, R>(i)) * cu + wi * (R(4.5) * cu * cu - R(1.5) * uu)),
                      0x80000000u);
       }
 #pragma unroll
@@ -1625,7 +1666,7 @@ __global__ void k_fields(Grid g, Phys<RT<S>> ph, const S* __restrict__ f,
     }
     if (which == 1) {
       const R fB0 = ORIG ? R(0) : fB_dir<L, R>(0, tp, ph.inv_tau_f);
-      out[s] = double(pressure<L, R>(ph, fv, u, F, fB0));
+      out[s] = p_of_part<L, R>(pressure<L, R>(ph, fv, u, F, fB0));
     } else if (which == 2) {
 #pragma unroll
       for (int k = 0; k < C; ++k) out[s * C + k] = double(A[k]);

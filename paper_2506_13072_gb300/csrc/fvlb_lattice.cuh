@@ -349,7 +349,41 @@ struct V2Layout {
   static constexpr bool on = Store<S>::V2;
 };
 
-// velocity part of f^eq: e_i(u) = w_i (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+// 3 w_i as the coefficient of the first-order terms (c_i.u, c_i.F) of the
+// flow equilibrium and the Guo forcing, chosen so that the lattice's second
+// moment sum_i (3 w_i) c_ia c_ib = delta_ab holds exactly in R.  With each
+// 3 w_i rounded on its own, FP32 gives (1 + 7.45e-9) delta_ab in both
+// lattices, so every collision adds that fraction of rho u and F to the
+// momentum, which over 10^4-10^5 steps of a channel flow was the largest
+// FP32 error against FP64.  One class of directions (axis or diagonal)
+// takes the rounded value, the other the remainder, whichever of the two
+// is exact in R; FP64 keeps the plain 3 w_i.
+template <class L>
+__host__ __device__ constexpr int n_diag_x() { return L::D == 2 ? 4 : 8; }
+template <class L, class R>
+__host__ __device__ constexpr double w3(int i) {
+  if (i == 0) return 0.0;
+  if (std::is_same<R, double>::value) return 3.0 * L::w(i);
+  const bool axis = cc<L>(i, 0) * cc<L>(i, 0) + cc<L>(i, 1) * cc<L>(i, 1) +
+                        cc<L>(i, 2) * cc<L>(i, 2) == 1;
+  double a = (double)(R)(3.0 * L::w(1));
+  double d = (1.0 - 2.0 * a) / n_diag_x<L>();
+  if ((double)(R)d != d) {
+    d = (double)(R)(3.0 * L::w(L::Q - 1));
+    a = (1.0 - n_diag_x<L>() * d) / 2.0;
+  }
+  return axis ? a : d;
+}
+template <class L, class R>
+__host__ __device__ constexpr bool w3_exact() {
+  const double a = w3<L, R>(1), d = w3<L, R>(L::Q - 1);
+  return (double)(R)a == a && (double)(R)d == d && 2.0 * a + n_diag_x<L>() * d == 1.0;
+}
+static_assert(w3_exact<D2Q9, float>() && w3_exact<D3Q19, float>(),
+              "first-order coefficients must carry the exact second moment in FP32");
+
+// velocity part of f^eq: e_i(u) = w_i (3 c.u + 4.5 (c.u)^2 - 1.5 u.u), with
+// w3<L, R>(i) for 3 w_i (so that sum_i c_i e_i(u) = u holds in R)
 template <class L, class R>
 __device__ __forceinline__ R feq_u(int i, const R (&u)[L::D]) {
   R cu = R(0), uu = R(0);
@@ -360,7 +394,81 @@ __device__ __forceinline__ R feq_u(int i, const R (&u)[L::D]) {
     if (c == -1) cu -= u[a];
     uu += u[a] * u[a];
   }
-  return R(L::w(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+  return R(w3<L, R>(i)) * cu + R(L::w(i)) * (R(4.5) * cu * cu - R(1.5) * uu);
+}
+
+// Sum of the weights as rounded to the working precision R, minus one
+// (exact in double: the rounded weights have few enough bits).  FP32:
+// 7.45e-9 (D2Q9), 1.49e-8 (D3Q19).  A collision whose equilibrium part is
+// w_i alpha moves the zeroth moment by alpha times this at every step; the
+// stress collisions take it back out of their rest population.
+template <class L, class R>
+__host__ __device__ constexpr double weight_sum_excess() {
+  double s = 0.0;
+  for (int i = 0; i < L::Q; ++i) s += (double)(R)L::w(i);
+  return s - 1.0;
+}
+
+// Pressure part of the flow equilibrium, lam_i p (lam_0 = 3 (w_0 - 1),
+// lam_i = 3 w_i), with p = c_s^2 / (1 - w_0) S and S the bracket of the
+// pressure formula (Sec. 2.2, Appendix B).  The next step's S sums the
+// non-rest populations, so the equilibrium gives S back times
+// (sum_{i>=1} lam_i) / (3 (1 - w_0)), which with FP32 constants is 1 + 4.3e-8
+// (D2Q9) or 1 + 3.0e-8 (D3Q19): a gain on the pressure at every collision.
+// In FP32 the part is formed as nu_i T with nu_i = w_i / w_1 (1 on the
+// axes, 1/4 (D2Q9) or 1/2 (D3Q19) on the diagonals, nu_0 = -K) and
+// T = S / K, K = (1 - w_0) / w_1 (5, 12), by a correctly rounded division:
+// every nu_i is exact and sum_{i>=1} nu_i = K, so nothing is gained or lost
+// beyond unbiased rounding.  FP64 keeps lam_i and p.
+// (the ratios are multiples of 1/4; rounding removes the FP64 quotients' error)
+__host__ __device__ constexpr double quarter(double x) {
+  return (double)(long long)(x * 4.0 + (x >= 0.0 ? 0.5 : -0.5)) / 4.0;
+}
+template <class L, class R>
+__host__ __device__ constexpr double p_coef(int i) {
+  if (std::is_same<R, double>::value) return i == 0 ? (L::w(0) - 1.0) * 3.0 : L::w(i) * 3.0;
+  return quarter(i == 0 ? (L::w(0) - 1.0) / L::w(1) : L::w(i) / L::w(1));
+}
+template <class L, class R>
+__device__ __forceinline__ R p_part(R S) {
+  if constexpr (std::is_same<R, double>::value) return R(1.0 / (3.0 * (1.0 - L::w(0)))) * S;
+  else return S / R(-p_coef<L, R>(0));
+}
+// the same from p itself (initial state): p / (3 w_1)
+template <class L, class R>
+__device__ __forceinline__ R p_part_of_p(R p) {
+  if constexpr (std::is_same<R, double>::value) return p;
+  else return p / R(quarter(1.0 / (3.0 * L::w(1))));
+}
+// p from the pressure variable (in FP64, for output)
+template <class L, class R>
+__device__ __forceinline__ double p_of_part(R t) {
+  if constexpr (std::is_same<R, double>::value) return t;
+  else return double(t) * quarter(1.0 / (3.0 * L::w(1)));
+}
+template <class L, class R>
+__host__ __device__ constexpr bool p_coef_exact() {
+  double k = 0.0;
+  for (int i = 1; i < L::Q; ++i) {
+    if ((double)(R)p_coef<L, R>(i) != p_coef<L, R>(i)) return false;
+    k += p_coef<L, R>(i);
+  }
+  return k == -p_coef<L, R>(0) && (double)(R)k == k;
+}
+static_assert(p_coef_exact<D2Q9, float>() && p_coef_exact<D3Q19, float>(),
+              "pressure coefficients must be exact in FP32 and sum to K");
+
+// the same with |u|^2 given
+template <class L, class R>
+__device__ __forceinline__ R feq_u(int i, const R (&u)[L::D], R uu) {
+  R cu = R(0);
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    const int c = cc<L>(i, a);
+    if (c == 1) cu += u[a];
+    if (c == -1) cu -= u[a];
+  }
+  return R(w3<L, R>(i)) * cu + R(L::w(i)) * (R(4.5) * cu * cu - R(1.5) * uu);
 }
 
 // The FP32 arrays that follow the 16-bit populations: U[D][pitch] after

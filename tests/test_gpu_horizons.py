@@ -26,12 +26,14 @@ def test_four_roll_20k_steps(Wi):
     compare(pr, 20000, FP64, 1e-12, chunks=4)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (FP32, 5e-5)])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (FP32, 2e-5)])
 def test_poiseuille_to_steady_state(prec, tol):
-    """FP32: the steady state of the FP32 iteration sits where its own
-    rounding balances, measured 3.6e-5 (u), 1.1e-5 (tau_p) from the FP64
-    oracle's after 30 000 steps; the bound 5e-5 is that measurement, and the
-    1000-step start-up of the same channel is held to 1e-5."""
+    """FP64 within 1e-12 of the oracle all the way to the steady state, and
+    both forms on the closed form.  FP32: a steady flow rounds the same way
+    at every step, so its rounding acts like a constant body force whose
+    response the slow channel amplifies by its viscous time (L^2 / nu, some
+    10^4 steps); measured 1.03e-5 (u), 1.75e-5 (tau_p) at 30 000 steps, held
+    to 2e-5.  The same channel over 4000 steps is held to 1e-5."""
     pr = W.poiseuille(L=32, nx=8, Wi=1.0, beta=0.1)
     compare(pr, 30000, prec, tol, chunks=5, fields=("u", "tau_p", "A"))
     s = gpu_sim(pr, prec)
