@@ -392,7 +392,7 @@ int fvlb_batch_destroy(fvlb_batch_t b); /* NULL-safe */
  * only]) to y = lambda chi [C]: D2Q9 8 -> 64 -> 64 -> 3, D3Q19
  * 15 -> 64 -> 64 -> 6, GELU (tanh form).  It is trained on the GPU (FP32
  * master weights, Adam) on pairs that the plain method's state provides, and
- * runs in the step with BF16 weights on the tensor cores (FP32 accumulate);
+ * runs in the step with FP16 weights on the tensor cores (FP32 accumulate);
  * per node, if ||chi_net - chi|| > tol ||chi|| the analytic chi is used.
  * ------------------------------------------------------------------------- */
 
@@ -428,7 +428,7 @@ int fvlb_mlp_set_params(fvlb_mlp_t m, const float *host, size_t count);
 int fvlb_mlp_grad(fvlb_mlp_t m, const float *x, const float *y, long n, float *grad,
                   double *loss);
 
-/* Tensor-core inference (BF16 weights, FP32 accumulate) of n host inputs. */
+/* Tensor-core inference (FP16 weights, FP32 accumulate) of n host inputs. */
 int fvlb_mlp_infer(fvlb_mlp_t m, const float *x, long n, float *y);
 
 const char *fvlb_mlp_last_error(fvlb_mlp_t m);

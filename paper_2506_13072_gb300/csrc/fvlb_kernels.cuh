@@ -433,7 +433,7 @@ struct FusedShape {
 template <int NG, int C, int NS>
 struct ClosureSmem {
   MlpPacked P;
-  __nv_bfloat16 X[NG][32][24];
+  __half X[NG][32][24];
   float Y[NG][32][8];
   float chi[C][NS];
 };
@@ -995,7 +995,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         if (mine) {
 #pragma unroll
           for (int q = 0; q < 16; q += 2)
-            *reinterpret_cast<uint32_t*>(&cls.X[grp][lane][q]) = pack_bf16x2(xin[q], xin[q + 1]);
+            *reinterpret_cast<uint32_t*>(&cls.X[grp][lane][q]) = pack_f16x2(xin[q], xin[q + 1]);
         }
         __syncwarp();
         mlp_tile(cls.P, cls.X[grp], cls.Y[grp], k);

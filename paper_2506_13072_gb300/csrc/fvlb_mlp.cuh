@@ -7,8 +7,11 @@
 // IN -> 64 -> 64 -> OUT (D2Q9: 8 -> 3, D3Q19: 15 -> 6), GELU in its tanh
 // form.  Training keeps FP32 master weights (per-sample forward/backward on
 // CUDA cores, deterministic block reductions, Adam); inference packs the
-// weights to BF16 and runs each layer of 32 nodes on the tensor cores with
-// mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  The products are
+// weights to FP16 and runs each layer of 32 nodes on the tensor cores with
+// mma.sync m16n8k16 (FP16 operands, FP32 accumulation), the GELU of each
+// pair of hidden units in packed FP16 arithmetic (half the instructions of
+// two FP32 evaluations; the activations are FP16 operands of the next
+// layer in any case).  The products are
 // 16 x 16 x 64 and 16 x 64 x 64 per warp (two warps per 32-node group, one
 // m16 tile each), fused into the collision of the nodes the group already
 // holds; the register-level mma keeps them there (a tcgen05 tile would need
@@ -16,7 +19,7 @@
 // product).
 #pragma once
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace fvlb {
@@ -46,36 +49,46 @@ struct MlpParams {
   static constexpr int N = B3 + OUT;
 };
 
-// Packed inference weights (BF16 rows padded so that the 32-bit fragment
+// Packed inference weights (FP16 rows padded so that the 32-bit fragment
 // loads of a warp hit 32 distinct shared-memory banks) and FP32 biases.
 struct __align__(16) MlpPacked {
-  __nv_bfloat16 W1[kMlpH][24];  // [n][k], k < 16 (inputs zero-padded to 16)
-  __nv_bfloat16 W2[kMlpH][72];  // [n][k], k < 64
-  __nv_bfloat16 W3[8][72];      // [n][k], n < OUT (rows beyond OUT are zero)
+  __half W1[kMlpH][24];  // [n][k], k < 16 (inputs zero-padded to 16)
+  __half W2[kMlpH][72];  // [n][k], k < 64
+  __half W3[8][72];      // [n][k], n < OUT (rows beyond OUT are zero)
   float b1[kMlpH], b2[kMlpH], b3[8];
 };
 
-__device__ __forceinline__ float gelu_fast(float z) {
-  float t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.7978845608028654f * (z + 0.044715f * z * z * z)));
-  return 0.5f * z * (1.0f + t);
+__device__ __forceinline__ uint32_t h2_bits(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+  return h2_bits(__floats2half2_rn(lo, hi));
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
+// GELU in its tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
+// of the pair (lo, hi), in packed FP16; returns the packed FP16 results.
+// Beyond |z| ~ 256 the cube overflows to +-inf, whose tanh is +-1, so the
+// result is z or 0 as GELU's limits are.
+__device__ __forceinline__ uint32_t gelu_f16x2(float lo, float hi) {
+  const __half2 z = __floats2half2_rn(lo, hi);
+  const __half2 z2 = __hmul2(z, z);
+  const __half2 in = __hfma2(__hmul2(__float2half2_rn(0.044715f), z2), z, z);
+  const __half2 arg = __hmul2(__float2half2_rn(0.7978845608028654f), in);
+  uint32_t t;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h2_bits(arg)));
+  const __half2 hz = __hmul2(__float2half2_rn(0.5f), z);
+  return h2_bits(__hfma2(hz, *reinterpret_cast<const __half2*>(&t), hz));
 }
 
 __device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                           uint32_t b1) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
       "{%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) {
+__device__ __forceinline__ uint32_t lds32(const __half* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
 
@@ -89,8 +102,8 @@ __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) {
 // The accumulators of two adjacent n8 tiles form the A fragment of the
 // next layer's k16 tile, so hidden activations never leave registers; the
 // layers are interleaved so that only one layer-1 output (16 registers of
-// packed BF16) and one pair of layer-2 tiles are live at a time.
-__device__ __forceinline__ void mlp_tile(const MlpPacked& P, const __nv_bfloat16 (*X)[24],
+// packed FP16) and one pair of layer-2 tiles are live at a time.
+__device__ __forceinline__ void mlp_tile(const MlpPacked& P, const __half (*X)[24],
                                          float (*Y)[8], int mt) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
@@ -111,10 +124,10 @@ __device__ __forceinline__ void mlp_tile(const MlpPacked& P, const __nv_bfloat16
     mma_16816(h0, a, lds32(&P.W1[2 * kt * 8 + g][2 * t]), lds32(&P.W1[2 * kt * 8 + g][2 * t + 8]));
     mma_16816(h1, a, lds32(&P.W1[(2 * kt + 1) * 8 + g][2 * t]),
               lds32(&P.W1[(2 * kt + 1) * 8 + g][2 * t + 8]));
-    a2[kt][0] = pack_bf16x2(gelu_fast(h0[0]), gelu_fast(h0[1]));
-    a2[kt][1] = pack_bf16x2(gelu_fast(h0[2]), gelu_fast(h0[3]));
-    a2[kt][2] = pack_bf16x2(gelu_fast(h1[0]), gelu_fast(h1[1]));
-    a2[kt][3] = pack_bf16x2(gelu_fast(h1[2]), gelu_fast(h1[3]));
+    a2[kt][0] = gelu_f16x2(h0[0], h0[1]);
+    a2[kt][1] = gelu_f16x2(h0[2], h0[3]);
+    a2[kt][2] = gelu_f16x2(h1[0], h1[1]);
+    a2[kt][3] = gelu_f16x2(h1[2], h1[3]);
   }
   // layers 2 (64 -> 64) and 3 (64 -> 8, OUT used): each pair of layer-2
   // n-tiles is one layer-3 k-tile, accumulated as soon as it is ready
@@ -136,10 +149,8 @@ __device__ __forceinline__ void mlp_tile(const MlpPacked& P, const __nv_bfloat16
       mma_16816(h1, a2[kt], lds32(&P.W2[(2 * k3 + 1) * 8 + g][kt * 16 + 2 * t]),
                 lds32(&P.W2[(2 * k3 + 1) * 8 + g][kt * 16 + 2 * t + 8]));
     }
-    const uint32_t a3[4] = {pack_bf16x2(gelu_fast(h0[0]), gelu_fast(h0[1])),
-                            pack_bf16x2(gelu_fast(h0[2]), gelu_fast(h0[3])),
-                            pack_bf16x2(gelu_fast(h1[0]), gelu_fast(h1[1])),
-                            pack_bf16x2(gelu_fast(h1[2]), gelu_fast(h1[3]))};
+    const uint32_t a3[4] = {gelu_f16x2(h0[0], h0[1]), gelu_f16x2(h0[2], h0[3]),
+                            gelu_f16x2(h1[0], h1[1]), gelu_f16x2(h1[2], h1[3])};
     mma_16816(y, a3, lds32(&P.W3[g][k3 * 16 + 2 * t]), lds32(&P.W3[g][k3 * 16 + 2 * t + 8]));
   }
   Y[r0][2 * t] = y[0];
@@ -149,7 +160,7 @@ __device__ __forceinline__ void mlp_tile(const MlpPacked& P, const __nv_bfloat16
 }
 
 // Both m-tiles of 32 rows (one warp).
-__device__ __forceinline__ void mlp_warp(const MlpPacked& P, const __nv_bfloat16 (*X)[24],
+__device__ __forceinline__ void mlp_warp(const MlpPacked& P, const __half (*X)[24],
                                          float (*Y)[8]) {
   mlp_tile(P, X, Y, 0);
   mlp_tile(P, X, Y, 1);

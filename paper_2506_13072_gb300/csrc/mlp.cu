@@ -1,6 +1,6 @@
 // mlp.cu -- the learned stress closure: training-pair collection from the
 // plain method's state, GPU training of the network (hand-written forward,
-// backward and Adam kernels), BF16 packing, tensor-core inference, and the
+// backward and Adam kernels), FP16 packing, tensor-core inference, and the
 // fvlb_mlp_* C ABI.  Applying the network inside the step is in
 // k_step_fused (fvlb_set_closure).
 #include <cuda_runtime.h>
@@ -252,22 +252,22 @@ __global__ void k_mlp_update(float* __restrict__ prm, float* __restrict__ mo,
   }
 }
 
-// FP32 master parameters -> packed BF16 inference weights
+// FP32 master parameters -> packed FP16 inference weights
 template <int IN, int OUT>
 __global__ void k_mlp_pack(const float* __restrict__ prm, MlpPacked* __restrict__ P) {
   using PP = MlpParams<IN, OUT>;
   constexpr int H = kMlpH;
   for (int e = threadIdx.x; e < H * 24; e += blockDim.x) {
     const int n = e / 24, k = e % 24;
-    P->W1[n][k] = __float2bfloat16_rn(k < IN ? prm[PP::W1 + n * IN + k] : 0.f);
+    P->W1[n][k] = __float2half_rn(k < IN ? prm[PP::W1 + n * IN + k] : 0.f);
   }
   for (int e = threadIdx.x; e < H * 72; e += blockDim.x) {
     const int n = e / 72, k = e % 72;
-    P->W2[n][k] = __float2bfloat16_rn(k < H ? prm[PP::W2 + n * H + k] : 0.f);
+    P->W2[n][k] = __float2half_rn(k < H ? prm[PP::W2 + n * H + k] : 0.f);
   }
   for (int e = threadIdx.x; e < 8 * 72; e += blockDim.x) {
     const int n = e / 72, k = e % 72;
-    P->W3[n][k] = __float2bfloat16_rn(n < OUT && k < H ? prm[PP::W3 + n * H + k] : 0.f);
+    P->W3[n][k] = __float2half_rn(n < OUT && k < H ? prm[PP::W3 + n * H + k] : 0.f);
   }
   for (int e = threadIdx.x; e < H; e += blockDim.x) {
     P->b1[e] = prm[PP::B1 + e];
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const MlpPacked* __restrict__
                                                    const float* __restrict__ X, long long n,
                                                    float* __restrict__ Y) {
   __shared__ MlpPacked P;
-  __shared__ __nv_bfloat16 xs[4][32][24];
+  __shared__ __half xs[4][32][24];
   __shared__ float ys[4][32][8];
   mlp_load(P, Pg);
   __syncthreads();
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const MlpPacked* __restrict__
   for (long long base = (blockIdx.x * 4LL + w) * 32; base < n; base += gridDim.x * 128LL) {
     const long long r = base + lane;
     for (int k = 0; k < 24; ++k)
-      xs[w][lane][k] = __float2bfloat16_rn(r < n && k < IN ? X[r * IN + k] : 0.f);
+      xs[w][lane][k] = __float2half_rn(r < n && k < IN ? X[r * IN + k] : 0.f);
     __syncwarp();
     mlp_warp(P, xs[w], ys[w]);
     __syncwarp();

@@ -16,21 +16,18 @@ from gpu_common import compact, fvlb, tau_floor, gpu_sim, oracle_sim, rel_l2, ti
 pytestmark = pytest.mark.gpu
 
 
-def _bf16(a):
-    """Round to the nearest bfloat16 (ties to even), kept in float64."""
-    f = np.asarray(a, np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+def _f16(a):
+    """Round to the nearest IEEE half (ties to even), kept in float64."""
+    return np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
 
 
-def _forward_bf16(p, x):
-    """The reference forward pass with operands rounded to bfloat16 as the
+def _forward_f16(p, x):
+    """The reference forward pass with operands rounded to FP16 as the
     tensor-core path does (weights, and each layer's input)."""
-    h = _bf16(x)
-    h = M.gelu(h @ _bf16(p["W1"]).T + p["b1"])
-    h = M.gelu(_bf16(h) @ _bf16(p["W2"]).T + p["b2"])
-    return _bf16(h) @ _bf16(p["W3"]).T + p["b3"]
+    h = _f16(x)
+    h = M.gelu(h @ _f16(p["W1"]).T + p["b1"])
+    h = M.gelu(_f16(h) @ _f16(p["W2"]).T + p["b2"])
+    return _f16(h) @ _f16(p["W3"]).T + p["b3"]
 
 
 @pytest.mark.parametrize("lattice", [9, 19])
@@ -48,7 +45,7 @@ def test_tensor_core_inference(lattice):
     y = net.infer(x).astype(np.float64)
     exact, _ = M.forward(p32, x.astype(np.float64))
     assert rel_l2(y, exact, 1e-30) < 3e-2
-    assert rel_l2(y, _forward_bf16(p32, x), 1e-30) < 5e-3
+    assert rel_l2(y, _forward_f16(p32, x), 1e-30) < 5e-3
     net.close()
 
 
