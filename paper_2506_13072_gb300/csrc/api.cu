@@ -71,6 +71,7 @@ struct fvlb_s {
   fvlb_mlp_t mlp = nullptr; // learned closure, or null
   double cl_tol = 1e-2;
   unsigned long long* cl_count = nullptr;  // [0] network nodes, [1] fallbacks
+  unsigned* dev_err = nullptr;  // bounded device waits that ran out (bit 0: staging copies)
   int scheme = FVLB_SCHEME_PRESENT;
   void* taup = nullptr;     // original scheme: polymer stress working array
   void* fdiv = nullptr;     // original scheme: its divergence (fused variant)
@@ -138,6 +139,7 @@ void free_all(fvlb_t h) {
   h->chi = h->ubuf = h->tables = nullptr;
   h->part = h->red = h->fbuf = nullptr;
   h->cl_count = nullptr;
+  h->dev_err = nullptr;
   h->taup = nullptr;
   h->fdiv = nullptr;
   h->allocated = false;
@@ -178,6 +180,7 @@ StepDesc make_desc(fvlb_t h) {
   d.fdiv = h->fdiv;
   d.model = h->model;
   d.mpar = h->mpar;
+  d.err = h->dev_err;
   double c = 0.0;
   if (h->force.kind == FVLB_FORCE_CONST) c = 1.0;
   if (h->force.kind == FVLB_FORCE_COSINE) c = std::cos(h->force.omega * (double)h->t);
@@ -206,9 +209,11 @@ int allocate(fvlb_t h) {
   h->part = static_cast<double*>(dev_alloc(h, sizeof(double) * 8 * (size_t)nparts));
   h->red = static_cast<double*>(dev_alloc(h, sizeof(double) * 8));
   h->cl_count = static_cast<unsigned long long*>(dev_alloc(h, 2 * sizeof(unsigned long long)));
+  h->dev_err = static_cast<unsigned*>(dev_alloc(h, sizeof(unsigned)));
   bool ok = h->f[0] && h->f[1] && h->h[0] && h->h[1] && h->chi && h->ubuf && h->part && h->red &&
-            h->cl_count;
+            h->cl_count && h->dev_err;
   if (ok && cudaMemset(h->cl_count, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) ok = false;
+  if (ok && cudaMemset(h->dev_err, 0, sizeof(unsigned)) != cudaSuccess) ok = false;
   // 16-bit forms: the i = 0 slots of the 16-bit stress arrays are never
   // used (the rest populations are FP32); zero them once so that checkpoint
   // images hold no leftover bytes
@@ -285,6 +290,8 @@ int run_init(fvlb_t h, const double* u0, const double* p0, const double* A0) {
     d.stream = h->stream;
     e = h->lattice == FVLB_D2Q9 ? fvlb::init_d2q9(d) : fvlb::init_d3q19(d);
   }
+  // a new state: forget the time-outs of the old one
+  if (e == cudaSuccess && h->dev_err) e = cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (tmp) dev_free(h, tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "initialisation");
@@ -534,6 +541,19 @@ static int check_poll(fvlb_t h, bool wait) {
   return FVLB_OK;
 }
 
+// The device's record of bounded waits that ran out (set by a step kernel
+// whose staged copies did not arrive within its time limit; the state is
+// then invalid until the fields are initialised again).  Synchronous.
+static int wait_check(fvlb_t h) {
+  if (!h->dev_err) return FVLB_OK;
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->dev_err, sizeof v, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "device wait record");
+  if (v) return fail(h, FVLB_ETIMEOUT, "a step kernel's staged copies did not arrive in time; the state is invalid");
+  return FVLB_OK;
+}
+
 static int unstable_fail(fvlb_t h) {
   return fail(h, FVLB_EUNSTABLE,
               ("non-finite values in the state (periodic check at step " +
@@ -609,6 +629,10 @@ int fvlb_status(fvlb_t h, int wait) {
   if (!h) return fail(nullptr, FVLB_EINVAL, "NULL handle");
   int r = check_poll(h, wait != 0);
   if (r != FVLB_OK) return r;
+  if (wait) {
+    r = wait_check(h);
+    if (r != FVLB_OK) return r;
+  }
   if (h->bad_t >= 0) return unstable_fail(h);
   return FVLB_OK;
 }
@@ -636,7 +660,7 @@ int fvlb_fields(fvlb_t h, int which, double* host_out, size_t count) {
     e = cudaMemcpyAsync(host_out, h->fbuf, sizeof(double) * need, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_fields");
-  return FVLB_OK;
+  return wait_check(h);
 }
 
 int fvlb_reduce(fvlb_t h, double out[8]) {
@@ -654,6 +678,8 @@ int fvlb_reduce(fvlb_t h, double out[8]) {
     e = cudaMemcpyAsync(out, h->red, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_reduce");
+  r = wait_check(h);
+  if (r != FVLB_OK) return r;
   if (out[6] > 0) return fail(h, FVLB_EUNSTABLE, "fvlb_reduce: non-finite values in the state");
   return FVLB_OK;
 }
@@ -794,6 +820,7 @@ int fvlb_load_state(fvlb_t h, const void* host_buf, size_t bytes) {
   cudaError_t e = cudaMemcpyAsync(h->f[h->cur], p, bf, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->h[h->cur], p + bf, bh, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->chi, p + bf + bh, bc, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && h->dev_err) e = cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "fvlb_load_state");
   h->first = hd.first;

@@ -59,6 +59,7 @@ struct StepDesc {
   void* fdiv;           // original scheme, fused variant: D * pitch working-precision values
   int model;            // constitutive model (0 Oldroyd-B, 1 Giesekus, 2 / 3 PTT)
   double mpar;          // its parameter
+  unsigned* err;        // device word: bounded waits that ran out (bit 0: staging copies)
 };
 
 struct InitDesc {

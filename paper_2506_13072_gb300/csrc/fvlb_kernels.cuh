@@ -17,6 +17,8 @@
 // velocity halo suffices.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the type only; maps are encoded on the host)
+
 #include <type_traits>
 
 #include "fvlb_lattice.cuh"
@@ -48,6 +50,91 @@ template <int N>
 __device__ __forceinline__ void cp_wait_group() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+// Bulk tensor copies (TMA) into shared memory, completed on an mbarrier.
+// A warp's lane 0 arms the barrier with the byte count of its copies and
+// issues them; every lane of the warp waits for the barrier's phase.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the copy engine
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Wait for the phase of parity `parity` to complete, for at most about 2 s;
+// on time-out record bit 0 in *err (when given) and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > 2000000000ull) {
+      if (err) atomicOr(err, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+// order this thread's earlier shared-memory accesses before later accesses
+// of the copy engine to the same memory
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2),
+      "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Tensor maps of one launch's staged arrays (the fused step's copies of a
+// warp's row of nodes into its stage buffer), encoded on the host; `on` = 0:
+// the warps copy with cp.async instead.  Dimension 0 is the node index
+// within a population array (x fastest, `pitch` long), so a box of BX
+// nodes is one warp's row; the arrays must start on 16-byte boundaries and
+// a box's first node must lie on one (nx a multiple of 16 / element size).
+struct StageMaps {
+  CUtensorMap h;    // h[C Q][pitch]; box BX x Q: component k's rows k Q ..
+  CUtensorMap f3;   // f as [J][C][pitch]; box BX x 1 x J: rows k + j C, j < J
+  CUtensorMap f4;   // D3Q19: f rows 0, C, 2C, 3C as [4][pitch]; box BX x 4
+  CUtensorMap x;    // chi[C][pitch]; box BX x 1
+  CUtensorMap e0;   // 16-bit forms: FP32 rest stress populations h0[C][pitch]; box BX x 1
+  CUtensorMap u;    // 16-bit forms: FP32 velocities U[D][pitch]; box BX x D
+  int on;
+};
 
 // Make a pointer opaque to the compiler at this point of the program.  Used
 // to stop the 114 population addresses of a D3Q19 site from being computed
@@ -464,7 +551,7 @@ struct TileCfg {
   static constexpr int NS = Sh::NG * 32 * XN;     // nodes per plane tile
   static constexpr int NFM = Split<L>::NFMAX;
   static constexpr int NPP = Q + NFM;             // staged populations per thread
-  static constexpr int NCT = Sh::NCW * 32 * XN;   // stage columns
+  static constexpr int BX = 32 * XN;              // stage columns of one warp
   static constexpr int CP = C == 6 ? 8 : 4;
   static constexpr bool PF = (sizeof(S) == 4 || sizeof(S) == 2) && !CL;
   using CLS = typename std::conditional<CL, ClosureSmem<Sh::NG, C, NS>, NoClosureSmem>::type;
@@ -472,29 +559,38 @@ struct TileCfg {
   // 16-bit forms: the FP32 rest stress population of the thread's
   // component and the node's stored velocity U, staged beside the rest
   static constexpr bool V2 = Store<S>::V2;
-  static constexpr int NEX = V2 ? 1 + D : 1;
-  static constexpr size_t kStage1 =
-      PF ? sizeof(S) * NPP * NCT + sizeof(X) * NCT + (V2 ? sizeof(float) * NEX * NCT : 0) : 0;
+  static constexpr int NEX = 1 + D;
+  // One collision warp's stage buffer: its component's Q stress populations
+  // and its NFM flow populations (i = k + j C) of the warp's BX nodes, chi,
+  // and (16-bit forms) the FP32 rest population and U; every part starts
+  // on a 128-byte boundary, as a bulk tensor copy into it requires.
+  struct WStage0 {
+    alignas(128) S h[Q][BX];
+    alignas(128) S f[NFM][BX];
+    alignas(128) X chi[BX];
+  };
+  struct WStageV2 : WStage0 {
+    alignas(128) float ext[NEX][BX];
+  };
+  using WStage = typename std::conditional<V2, WStageV2, WStage0>::type;
+  static constexpr size_t kStage1 = PF ? sizeof(WStage) * Sh::NCW : 0;
   static constexpr size_t kEx1 = 2 * sizeof(R) * CP * NS;
-  // dynamic shared memory: several rows per thread, or a staged 2D tile
-  // (whose stage fills the static 48 KB and leaves no room for the
-  // double-buffered exchange or a third stage)
-  static constexpr bool kDynamic = XN > 1 || (PF && D == 2);
+  // dynamic shared memory: several rows per thread, a staged 2D tile or a
+  // staged 16-bit tile (whose stages fill the static 48 KB and leave no room
+  // for the double-buffered exchange or a third stage)
+  static constexpr bool kDynamic = XN > 1 || (PF && (D == 2 || V2));
   static constexpr size_t kLimit = kDynamic ? (MINB >= 3 ? 72 : 110) * 1024 : 48 * 1024;
   static constexpr int NST =
       (PF && kRing + sizeof(CLS) + 3 * kStage1 + 2 * kEx1 <= kLimit) ? 3 : 2;
   static constexpr int NBUF = (kRing + sizeof(CLS) + NST * kStage1 + 2 * kEx1 <= kLimit) ? 2 : 1;
-  using Stage = typename std::conditional<PF, S[NST][NPP][NCT], int>::type;
-  using StageX = typename std::conditional<PF, X[NST][NCT], int>::type;
-  using StageE = typename std::conditional<PF && V2, float[NST][NEX][NCT], int>::type;
+  using Stage = typename std::conditional<PF, WStage[NST][Sh::NCW], int>::type;
   struct Smem {
     Vel<R, D> ring[4][Sh::NE];                    // velocity of planes m-1 .. m+2
     alignas(16) R sAd[NBUF][NS][CP];              // A - I of the tile nodes
     alignas(16) R sPf[NBUF][NS][CP];              // partial sums of f_{i != 0}
     CLS cls;                                      // learned closure (CL only)
-    alignas(16) Stage stage;
-    alignas(16) StageX stage_x;
-    alignas(16) StageE stage_e;
+    alignas(128) Stage stage;
+    uint64_t bar[PF ? NST : 1][Sh::NCW];          // bulk-copy barriers of the stage buffers
   };
   static constexpr size_t kDynamicBytes = kDynamic ? sizeof(Smem) : 0;
 };
@@ -506,7 +602,7 @@ template <class L, class S, int GX, int TY, bool WALLS, bool FW, bool CL = false
           bool ORIG = false, int MINB = 2>
 __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
                                            const Bufs<S>& b, int mchunk, int bx, int by,
-                                           int bz) {
+                                           int bz, const StageMaps* tm = nullptr) {
   using R = RT<S>;
   using X = typename Store<S>::X;
   using Sh = FusedShape<L, GX, TY, FW, XN>;
@@ -517,7 +613,6 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   constexpr int NFM = Cfg::NFM, NPP = Cfg::NPP, NST = Cfg::NST, NBUF = Cfg::NBUF;
   constexpr bool PF = Cfg::PF;
   constexpr bool PAIR = sizeof(S) == 2;
-  constexpr int WC = NCW * 32;          // stage columns of one node row
   static_assert(D == 3 || TY == 1, "2D tiles are one row high");
   static_assert(FW || NE <= NCW * 32, "in-collision fill: one ring slot per thread");
   static_assert(XN == 1 || (FW && PF), "several nodes per thread: fill warps, staged storage");
@@ -525,7 +620,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   using Sm = typename Cfg::Smem;
   Sm* smp;
   if constexpr (Cfg::kDynamic) {
-    extern __shared__ __align__(16) unsigned char fvlb_tile_smem[];
+    extern __shared__ __align__(128) unsigned char fvlb_tile_smem[];
     smp = reinterpret_cast<Sm*>(fvlb_tile_smem);
   } else {
     __shared__ Sm tile_smem;
@@ -536,12 +631,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   auto& sPf = smp->sPf;
   auto& cls = smp->cls;
   auto& stage = smp->stage;
-  auto& stage_x = smp->stage_x;
-  auto& stage_e = smp->stage_e;
-  (void)stage_e;
   (void)cls;
   (void)stage;
-  (void)stage_x;
 
   const int nx = g.nx, ny = g.ny;
   const int nm = (D == 3) ? g.nz : g.ny;
@@ -710,7 +801,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 
   // ---------------- collision warps ------------------------------------------
   // Node n < XN of this thread: x + 32 n, sAd / sPf row node + 32 n, ring
-  // slot e_own + 32 n, stage column tid + n * WC.
+  // slot e_own + 32 n, column 32 n + lane of the warp's stage buffer.
   const int lane = tid & 31;
   const int grp = warp / C;
   const int k = warp - grp * C;         // stress component of this thread
@@ -742,6 +833,26 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   auto wide_n = [&](int n) {
     return PF && WIDE && yin && x0 + gxi * 32 * XN + 32 * n + 31 < nx && (nx % EPC) == 0;
   };
+  // Bulk tensor copies: lane 0 copies the warp's whole row of BX nodes of
+  // every staged array with one tensor copy per array group (the copy
+  // engine reads past nx into the next row, and fills with zeros past the
+  // end of the arrays); the row's first node must lie on a 16-byte
+  // boundary, which nx % EPC == 0 and the 32-node warp rows give.
+  constexpr int BX = 32 * XN;
+  constexpr int NJ = (Q - C) / C + 1;   // flow rows k + j C in range for every k
+  static_assert(Split<L>::nf(0) <= NJ + 1, "flow rows: NJ, or NJ + 1 for component 0");
+  const bool tma = PF && tm != nullptr && tm->on && pf && (nx % EPC) == 0 &&
+                   ((x0 + gxi * 32 * XN) % EPC) == 0;
+  if constexpr (PF) {
+    if (tma) {
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NST; ++q) mbar_init(&smp->bar[q][warp], 1);
+        mbar_init_fence();
+      }
+      __syncwarp();
+    }
+  }
   // Issue the copies of plane q's populations of every node of this thread
   // into stage buffer st.  Every call by a thread that stages commits exactly
   // one group (empty past the end of the chunk), so a wait for all but the
@@ -749,6 +860,28 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   auto prefetch = [&](int q, int st) {
     if constexpr (PF) {
       if (!pf || !active) return;
+      auto& W = stage[st][warp];
+      if (tma) {
+        if (lane == 0 && q < m1) {
+          const int s0 = (D == 3) ? (q * ny + y) * nx + x0 + gxi * 32 * XN
+                                  : q * nx + x0 + gxi * 32 * XN;
+          constexpr int ES = (int)sizeof(S);
+          const int nfr = Split<L>::nf(k) > NJ ? NJ + 1 : NJ;
+          const unsigned bytes = (unsigned)((Q + nfr) * BX * ES + BX * 4 + (V2 ? (1 + D) * BX * 4 : 0));
+          uint64_t* bar = &smp->bar[st][warp];
+          fence_proxy_async();   // the warp's reads of this buffer (ordered by __syncwarp) first
+          mbar_arrive_expect_tx(bar, bytes);
+          tma_load_2d(&W.h[0][0], &tm->h, s0, k * Q, bar);
+          if (nfr > NJ) tma_load_2d(&W.f[0][0], &tm->f4, s0, 0, bar);
+          else tma_load_3d(&W.f[0][0], &tm->f3, s0, k, 0, bar);
+          tma_load_2d(&W.chi[0], &tm->x, s0, k, bar);
+          if constexpr (V2) {
+            tma_load_2d(&W.ext[0][0], &tm->e0, s0, k, bar);
+            tma_load_2d(&W.ext[1][0], &tm->u, s0, 0, bar);
+          }
+        }
+        return;
+      }
       if (q < m1) {
 #pragma unroll
         for (int n = 0; n < XN; ++n) {
@@ -756,65 +889,67 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           const long long sq = (D == 3) ? ((long long)q * ny + y) * nx + x + 32 * n
                                         : (long long)q * nx + x + 32 * n;
           const uint32_t sq32 = (uint32_t)sq;
-          const int col = tid + n * WC;
+          const int c = 32 * n + lane;          // this lane's column
           if (wide_n(n)) {
             constexpr int CPR = 32 / EPC;          // chunks per row of 32 nodes
             constexpr int NCP = NPP * CPR;         // population chunks
             constexpr int NCX = NCP + 32 * 4 / 16; // and chi (4-byte) chunks
             constexpr int NCH = NCX + (V2 ? 8 * (1 + D) : 0);  // and h0, U (16-bit forms)
             const uint32_t s0 = sq32 - (uint32_t)lane;  // node of lane 0
-            const int wb = col - lane;             // the row's stage columns
+            const int wb = 32 * n;                 // the row's stage columns
 #pragma unroll
             for (int jj = 0; jj < (NCH + 31) / 32; ++jj) {
-              const int c = lane + 32 * jj;
-              if (c < NCP) {
-                const int v = c / CPR, sub = c % CPR;
+              const int cc = lane + 32 * jj;
+              if (cc < NCP) {
+                const int v = cc / CPR, sub = cc % CPR;
                 const int i = v < Q ? v : k + (v - Q) * C;
                 const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + s0 + (uint32_t)(sub * EPC));
+                S* dst = (v < Q ? W.h[v < Q ? v : 0] : W.f[v < Q ? 0 : v - Q]) + wb + sub * EPC;
                 // (16-bit forms: the rest stress population is in FP32)
-                if (i < Q && !(V2 && v == 0)) cp_async<16>(&stage[st][v][wb + sub * EPC], src);
-              } else if (c < NCX) {
-                const int sub = c - NCP;
-                cp_async<16>(&stage_x[st][wb + sub * 4], b.chi + ((uint32_t)k * P32 + s0 + (uint32_t)(sub * 4)));
-              } else if (V2 && c < NCH) {
-                const int arr = (c - NCX) >> 3, sub = (c - NCX) & 7;
+                if (i < Q && !(V2 && v == 0)) cp_async<16>(dst, src);
+              } else if (cc < NCX) {
+                const int sub = cc - NCP;
+                cp_async<16>(&W.chi[wb + sub * 4], b.chi + ((uint32_t)k * P32 + s0 + (uint32_t)(sub * 4)));
+              } else if (V2 && cc < NCH) {
+                const int arr = (cc - NCX) >> 3, sub = (cc - NCX) & 7;
                 const float* src = arr == 0 ? h_ext<L>(b.h_in, P) + (uint32_t)k * P32
                                             : f_ext<L>(b.f_in, P) + (uint32_t)(arr - 1) * P32;
                 if constexpr (V2)
-                  cp_async<16>(&stage_e[st][arr][wb + sub * 4], src + s0 + (uint32_t)(sub * 4));
+                  cp_async<16>(&W.ext[arr][wb + sub * 4], src + s0 + (uint32_t)(sub * 4));
               }
             }
             continue;
           }
           if constexpr (PAIR) {
             // lanes 2j, 2j + 1 hold nodes sq, sq + 1 (x even, nx even)
-            const int par = tid & 1;
-            const int tb = col - par;
+            const int par = lane & 1;
+            const int tb = c - par;
             const uint32_t sp = sq32 - (uint32_t)par;
 #pragma unroll
             for (int jj = 0; jj < (NPP + 1) / 2; ++jj) {
               const int v = 2 * jj + par;
               const int i = v < Q ? v : k + (v - Q) * C;
               const S* src = (v < Q ? hin_k : b.f_in) + ((uint32_t)i * P32 + sp);
-              if (v < NPP && i < Q && !(V2 && v == 0)) cp_async<4>(&stage[st][v][tb], src);
+              if (v < NPP && i < Q && !(V2 && v == 0))
+                cp_async<4>((v < Q ? W.h[v < Q ? v : 0] : W.f[v < Q ? 0 : v - Q]) + tb, src);
             }
             if constexpr (V2) {   // the FP32 values of this lane's own node
-              cp_async<4>(&stage_e[st][0][col], h_ext<L>(b.h_in, P) + ((uint32_t)k * P32 + sq32));
+              cp_async<4>(&W.ext[0][c], h_ext<L>(b.h_in, P) + ((uint32_t)k * P32 + sq32));
 #pragma unroll
               for (int a = 0; a < D; ++a)
-                cp_async<4>(&stage_e[st][1 + a][col], f_ext<L>(b.f_in, P) + ((uint32_t)a * P32 + sq32));
+                cp_async<4>(&W.ext[1 + a][c], f_ext<L>(b.f_in, P) + ((uint32_t)a * P32 + sq32));
             }
           } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async<4>(&stage[st][i][col], hin_k + ((uint32_t)i * P32 + sq32));
+            for (int i = 0; i < Q; ++i) cp_async<4>(&W.h[i][c], hin_k + ((uint32_t)i * P32 + sq32));
 #pragma unroll
             for (int j = 0; j < NFM; ++j) {
               const int i = k + j * C;
-              if (i < Q) cp_async<4>(&stage[st][Q + j][col], b.f_in + ((uint32_t)i * P32 + sq32));
+              if (i < Q) cp_async<4>(&W.f[j][c], b.f_in + ((uint32_t)i * P32 + sq32));
             }
           }
           static_assert(sizeof(X) == 4, "chi is staged in 4-byte copies");
-          cp_async<4>(&stage_x[st][col], b.chi + ((uint32_t)k * P32 + sq32));
+          cp_async<4>(&W.chi[c], b.chi + ((uint32_t)k * P32 + sq32));
         }
       }
       cp_commit();
@@ -867,47 +1002,54 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           // synchronisation tells them that every lane has finished the
           // collision of plane m - 1, whose buffer (NST = 2) the next
           // copies overwrite.
-          if constexpr (NST == 3) cp_wait_group<1>();
-          else cp_wait_all();
-          if (PAIR || WIDE) __syncwarp(amask);
+          if (tma) {
+            mbar_wait(&smp->bar[st][warp], (unsigned)(((m - m0) / NST) & 1), ph.err);
+            __syncwarp(amask);
+          } else {
+            if constexpr (NST == 3) cp_wait_group<1>();
+            else cp_wait_all();
+            if (PAIR || WIDE) __syncwarp(amask);
+          }
           prefetch(m + NST - 1, st_ahead);
         } else {
           // no copies for this kernel: the nodes' own values into their own
           // stage columns
+          auto& W = stage[st][warp];
 #pragma unroll
           for (int n = 0; n < XN; ++n) {
             if (!active_n(n)) continue;
-            const int col = tid + n * WC;
+            const int c = 32 * n + lane;
             const uint32_t sn32 = s32 + 32u * n;
 #pragma unroll
-            for (int i = V2 ? 1 : 0; i < Q; ++i) stage[st][i][col] = hin_k[(uint32_t)i * P32 + sn32];
+            for (int i = V2 ? 1 : 0; i < Q; ++i) W.h[i][c] = hin_k[(uint32_t)i * P32 + sn32];
 #pragma unroll
             for (int j = 0; j < NFM; ++j) {
               const int i = k + j * C;
-              if (i < Q) stage[st][Q + j][col] = b.f_in[(uint32_t)i * P32 + sn32];
+              if (i < Q) W.f[j][c] = b.f_in[(uint32_t)i * P32 + sn32];
             }
-            stage_x[st][col] = b.chi[(uint32_t)k * P32 + sn32];
+            W.chi[c] = b.chi[(uint32_t)k * P32 + sn32];
             if constexpr (V2) {
-              stage_e[st][0][col] = h_ext<L>(b.h_in, P)[(uint32_t)k * P32 + sn32];
+              W.ext[0][c] = h_ext<L>(b.h_in, P)[(uint32_t)k * P32 + sn32];
 #pragma unroll
               for (int a = 0; a < D; ++a)
-                stage_e[st][1 + a][col] = f_ext<L>(b.f_in, P)[(uint32_t)a * P32 + sn32];
+                W.ext[1 + a][c] = f_ext<L>(b.f_in, P)[(uint32_t)a * P32 + sn32];
             }
           }
         }
+        auto& W = stage[st][warp];
 #pragma unroll
         for (int n = 0; n < XN; ++n) {
           if (!active_n(n)) continue;
-          const int col = tid + n * WC;
+          const int c = 32 * n + lane;
           R a = R(0), psum = R(0);
-          if constexpr (V2) a = stage_e[st][0][col];
-          else a = Store<S>::cvt(stage[st][0][col]);
+          if constexpr (V2) a = W.ext[0][c];
+          else a = Store<S>::cvt(W.h[0][c]);
 #pragma unroll
-          for (int i = 1; i < Q; ++i) a += Store<S>::cvt(stage[st][i][col]);
+          for (int i = 1; i < Q; ++i) a += Store<S>::cvt(W.h[i][c]);
 #pragma unroll
           for (int j = 0; j < NFM; ++j) {
             const int i = k + j * C;
-            if (i != 0 && i < Q) psum += Store<S>::cvt(stage[st][Q + j][col]);
+            if (i != 0 && i < Q) psum += Store<S>::cvt(W.f[j][c]);
           }
           // (16-bit forms: the sum of the scaled deviations s_i, i != 0;
           // the collision adds the sum of e_i(U), i != 0, = 1.5 w_0 |U|^2)
@@ -1035,7 +1177,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       const int xn = x + 32 * n;
       const int nd = node + 32 * n;
       const int eo = e_own + 32 * n;
-      const int col = tid + n * WC;
+      const int col = 32 * n + lane;      // column of the warp's stage buffer
       const uint32_t sn32 = s32 + 32u * n;
       R u[D];
       {
@@ -1059,7 +1201,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       if constexpr (V2) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          Us[a] = stage_e[st][1 + a][col];
+          Us[a] = stage[st][warp].ext[1 + a][col];
           UU += Us[a] * Us[a];
         }
         sumf += R(1.5 * L::w(0)) * UU;
@@ -1134,7 +1276,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
         }
       });
       R oldn = old;
-      if constexpr (PF) oldn = R(stage_x[st][col]);
+      if constexpr (PF) oldn = R(stage[st][warp].chi[col]);
       if (ph.first) oldn = chi_k;
       b.chi[(uint32_t)k * P32 + sn32] = X(chi_k);
       const R src = R(1.5) * chi_k - R(0.5) * oldn;
@@ -1253,8 +1395,8 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           }
           R hvi;
           if constexpr (PF) {
-            if constexpr (V2) hvi = i == 0 ? R(stage_e[st][0][col]) : Store<S>::cvt(stage[st][i][col]);
-            else hvi = Store<S>::cvt(stage[st][i][col]);
+            if constexpr (V2) hvi = i == 0 ? R(stage[st][warp].ext[0][col]) : Store<S>::cvt(stage[st][warp].h[i][col]);
+            else hvi = Store<S>::cvt(stage[st][warp].h[i][col]);
           } else {
             hvi = hv[i];
           }
@@ -1304,7 +1446,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
               const R Fi = ph.kf * (w3i * cF + wi * (R(9) * cF * cu - R(3) * Fu));
               const R fBi = fB_dir<L, R>(i, Ad, kB);
               R foi;
-              if constexpr (PF) foi = Store<S>::cvt(stage[st][Q + jj][col]);
+              if constexpr (PF) foi = Store<S>::cvt(stage[st][warp].f[jj][col]);
               else foi = fo[jj];
               if constexpr (V2) foi = foi * R(1.0f / Store<S>::KF) + feq_u<L, R>(i, Us, UU);
               const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
@@ -1337,9 +1479,10 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL = false,
           int XN = 1, bool ORIG = false>
 __global__ void __launch_bounds__(FusedShape<L, GX, TY, FW, XN>::NT, MINB)
-    k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk) {
+    k_step_fused(Grid g, Phys<RT<S>> ph, Bufs<S> b, int mchunk,
+                 const __grid_constant__ StageMaps tm) {
   fused_tile<L, S, GX, TY, WALLS, FW, CL, XN, ORIG, MINB>(g, ph, b, mchunk, blockIdx.x, blockIdx.y,
-                                                    blockIdx.z);
+                                                    blockIdx.z, &tm);
 }
 
 // ---------------------------------------------------------------------------

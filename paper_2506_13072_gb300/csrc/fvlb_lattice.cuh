@@ -305,6 +305,7 @@ struct Phys {
   const R* cys;       // cos(k y)
   int first;          // first step: chi of the previous step := chi
   uint32_t step;      // step counter (stochastic-rounding stream)
+  unsigned* err;      // bounded device waits that ran out (bit 0: staging copies), or null
   R lam;              // lambda
   const void* mlp;    // learned closure: packed network weights (or null)
   float cl_tol2;      // squared fallback tolerance of the learned closure

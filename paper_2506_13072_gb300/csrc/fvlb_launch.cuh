@@ -2,12 +2,17 @@
 // lattice's translation unit instantiates it once.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
-#include <cstdlib>
-#include <type_traits>
 
 #include "fvlb_internal.h"
 #include "fvlb_kernels.cuh"
@@ -55,7 +60,97 @@ Phys<R> make_phys(const StepDesc& d) {
   p.model = d.model;
   p.mpar = R(d.mpar);
   p.fdiv = nullptr;
+  p.err = d.err;
   return p;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library does not link the driver API); null when it is unavailable
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// One tiled map without swizzle or interleave; dims[0] runs over the nodes
+// of a population array, strides are the byte strides of dims 1 ...
+inline bool encode_map(CUtensorMap* m, CUtensorMapDataType t, int rank, const void* base,
+                       const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+  const auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, t, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tensor maps of a fused launch whose warps stage rows of BX nodes
+// (StageMaps in fvlb_kernels.cuh); `on` = 0 (the kernel's cp.async
+// staging) when a row start cannot lie on a 16-byte boundary, a buffer is
+// not 16-byte aligned, an encoding fails, or FVLB_STAGE_TMA=0.
+template <class L, class S>
+StageMaps stage_maps(const StepDesc& d, int BX) {
+  StageMaps m;
+  std::memset(&m, 0, sizeof m);
+  constexpr int Q = L::Q, C = L::C, D = L::D;
+  constexpr int NJ = (Q - C) / C + 1;
+  constexpr cuuint64_t es = sizeof(S);
+  if (tune_int("FVLB_STAGE_TMA", 1) == 0) return m;
+  if (((cuuint64_t)d.nx * es) % 16 != 0 || ((cuuint64_t)d.pitch * es) % 16 != 0) return m;
+  auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  if (!aligned(d.f_in) || !aligned(d.h_in) || !aligned(d.chi)) return m;
+  const CUtensorMapDataType t =
+      es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  const CUtensorMapDataType tf = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t P = (cuuint64_t)d.pitch;
+  const cuuint32_t bx = (cuuint32_t)BX;
+  bool ok = true;
+  {
+    const cuuint64_t dims[2] = {P, (cuuint64_t)C * Q}, st[1] = {P * es};
+    const cuuint32_t box[2] = {bx, (cuuint32_t)Q};
+    ok = ok && encode_map(&m.h, t, 2, d.h_in, dims, st, box);
+  }
+  {
+    const cuuint64_t dims[3] = {P, (cuuint64_t)C, (cuuint64_t)NJ}, st[2] = {P * es, C * P * es};
+    const cuuint32_t box[3] = {bx, 1, (cuuint32_t)NJ};
+    ok = ok && encode_map(&m.f3, t, 3, d.f_in, dims, st, box);
+  }
+  if (Split<L>::nf(0) > NJ) {
+    const cuuint64_t dims[2] = {P, (cuuint64_t)NJ + 1}, st[1] = {C * P * es};
+    const cuuint32_t box[2] = {bx, (cuuint32_t)NJ + 1};
+    ok = ok && encode_map(&m.f4, t, 2, d.f_in, dims, st, box);
+  }
+  {
+    static_assert(sizeof(typename Store<S>::X) == 4, "chi is staged as 4-byte values");
+    const cuuint64_t dims[2] = {P, (cuuint64_t)C}, st[1] = {P * 4};
+    const cuuint32_t box[2] = {bx, 1};
+    ok = ok && encode_map(&m.x, tf, 2, d.chi, dims, st, box);
+  }
+  if constexpr (Store<S>::V2) {
+    const char* h0 = static_cast<const char*>(d.h_in) + es * C * Q * P;
+    const char* U = static_cast<const char*>(d.f_in) + es * Q * P;
+    if (!aligned(h0) || !aligned(U)) return m;
+    {
+      const cuuint64_t dims[2] = {P, (cuuint64_t)C}, st[1] = {P * 4};
+      const cuuint32_t box[2] = {bx, 1};
+      ok = ok && encode_map(&m.e0, tf, 2, h0, dims, st, box);
+    }
+    {
+      const cuuint64_t dims[2] = {P, (cuuint64_t)D}, st[1] = {P * 4};
+      const cuuint32_t box[2] = {bx, (cuuint32_t)D};
+      ok = ok && encode_map(&m.u, tf, 2, U, dims, st, box);
+    }
+  }
+  m.on = ok ? 1 : 0;
+  return m;
 }
 
 inline int grid_stride_blocks(long long N, int threads, int sms) {
@@ -88,7 +183,7 @@ cudaError_t allow_dynamic_smem(K* kern, size_t bytes) {
 template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool CL, int XN,
           bool ORIG = false>
 cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
-                          const Bufs<S>& b, int mchunk) {
+                          const Bufs<S>& b, int mchunk, const StageMaps& tm) {
   constexpr int NT = FusedShape<L, GX, TY, FW, XN>::NT;
   constexpr size_t dyn = TileCfg<L, S, GX, TY, FW, CL, XN, MINB>::kDynamicBytes;
   auto kern = k_step_fused<L, S, GX, TY, MINB, WALLS, FW, CL, XN, ORIG>;
@@ -96,7 +191,7 @@ cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phy
     const cudaError_t e = allow_dynamic_smem(kern, dyn);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, NT, dyn, d.stream>>>(g, ph, b, mchunk);
+  kern<<<grid, NT, dyn, d.stream>>>(g, ph, b, mchunk, tm);
   return cudaGetLastError();
 }
 
@@ -117,15 +212,18 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   mchunk = std::min(mchunk, nm);
   nchunk = (nm + mchunk - 1) / mchunk;
   dim3 grid(bx, by, nchunk);
+  StageMaps tm;
+  std::memset(&tm, 0, sizeof tm);
   if constexpr (std::is_same<S, float>::value && XN == 1 && !ORIG) {
     if (d.mlp) {  // learned closure (FP32 storage only); two blocks per SM
-      if (d.walls) return launch_kernel<L, S, GX, TY, 2, true, FW, true, 1>(grid, d, g, ph, b, mchunk);
-      return launch_kernel<L, S, GX, TY, 2, false, FW, true, 1>(grid, d, g, ph, b, mchunk);
+      if (d.walls) return launch_kernel<L, S, GX, TY, 2, true, FW, true, 1>(grid, d, g, ph, b, mchunk, tm);
+      return launch_kernel<L, S, GX, TY, 2, false, FW, true, 1>(grid, d, g, ph, b, mchunk, tm);
     }
   }
+  if constexpr (TileCfg<L, S, GX, TY, FW, false, XN, MINB>::PF) tm = stage_maps<L, S>(d, 32 * XN);
   if (d.walls)
-    return launch_kernel<L, S, GX, TY, MINB, true, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk);
-  return launch_kernel<L, S, GX, TY, MINB, false, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk);
+    return launch_kernel<L, S, GX, TY, MINB, true, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk, tm);
+  return launch_kernel<L, S, GX, TY, MINB, false, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk, tm);
 }
 
 // The fused step in the shape measured fastest on GB300 (256^3 D3Q19, 2048^2

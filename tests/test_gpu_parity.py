@@ -148,8 +148,13 @@ def test_taylor_green_32(kernel, prec):
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("shape,walls", [((37, 19, 11), 0b100), ((5, 4, 6), 0b010),
-                                         ((33, 9, 3), 0b101), ((1, 1, 7), 0), ((8, 1, 1), 0)])
+                                         ((33, 9, 3), 0b101), ((1, 1, 7), 0), ((8, 1, 1), 0),
+                                         ((40, 7, 5), 0b010), ((24, 5, 9), 0b100),
+                                         ((68, 3, 4), 0b001)])
 def test_ragged_d3q19(kernel, prec, shape, walls):
+    """Ragged and degenerate grids; nx a multiple of 4 (8, 40, 24, 68) puts
+    the FP32 fused step on its bulk tensor copies, whose 64-node boxes run
+    past the row (and the grid) there."""
     nx, ny, nz = shape
     pr = W.Problem("r3", W.D3Q19, nx, ny, nz, 0.75, 0.1, 13.0, W.FORCE_CONST,
                    (1e-5, 2e-5, -1e-5), walls=walls)
@@ -192,6 +197,33 @@ def test_ragged_16bit(prec, bu, bt, shape, walls):
     _with_random(pr, seed=sum(shape) + walls)
     w = compare(pr, 20, prec, 1.0, chunks=2, fields=("u", "tau_p"))
     assert w["u"] <= bu and w["tau_p"] <= bt, w
+
+
+# The fused step stages each warp's populations either with bulk tensor
+# copies (one per array group, nx a multiple of 16 bytes' worth of nodes) or
+# with per-lane cp.async copies (FVLB_STAGE_TMA=0 forces these); the two
+# must give bitwise the same state.
+@pytest.mark.parametrize("prec", [FP32, FP16, BF16])
+@pytest.mark.parametrize("shape,walls", [((40, 6, 5), 0b010), ((64, 4, 3), 0), ((96, 7), 0b10),
+                                         ((136, 5), 0)])
+def test_stage_copies_bitwise(prec, shape, walls, monkeypatch):
+    if len(shape) == 3:
+        nx, ny, nz = shape
+        pr = W.Problem("r3", W.D3Q19, nx, ny, nz, 0.75, 0.1, 13.0, W.FORCE_CONST,
+                       (1e-5, 2e-5, -1e-5), walls=walls)
+    else:
+        nx, ny = shape
+        pr = W.Problem("r", W.D2Q9, nx, ny, 1, 0.7, 0.15, 11.0, W.FORCE_CONST,
+                       (1e-5, -2e-5, 0.0), walls=walls)
+    _with_random(pr, seed=sum(shape) + 3 * walls)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FVLB_STAGE_TMA", flag)
+        s = gpu_sim(pr, prec)
+        s.step(12)
+        out.append(np.concatenate([s.u().ravel(), s.tau_p().ravel(), s.p().ravel()]))
+        s.close()
+    assert np.array_equal(out[0], out[1])
 
 
 # ---------------------------------------------------------------------------
