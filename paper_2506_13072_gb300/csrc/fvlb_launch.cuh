@@ -228,10 +228,10 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
 
 // The fused step in the shape measured fastest on GB300 (256^3 D3Q19, 2048^2
 // D2Q9): 2D four 32-node groups x 3 components (384 threads, 2 blocks per
-// SM); 3D FP32 a 64-node row, each of the 6 component warps taking its two
-// 32-node halves in turn, + 4 halo fill warps (320 threads, 2 blocks per SM;
-// a 64-register cap for 3 blocks per SM measured slower); 3D 16-bit, FP64
-// and the learned closure one 32-node row.  ORIG: the original scheme's
+// SM); 3D FP32 and 16-bit a 64-node row, each of the 6 component warps
+// taking its two 32-node halves in turn, + 4 halo fill warps (320 threads, 2
+// blocks per SM; a 64-register cap for 3 blocks per SM measured slower); 3D
+// FP64 and the learned closure one 32-node row.  ORIG: the original scheme's
 // step (div tau_p from ph.fdiv in the body force, f^B off).
 template <class L, class S, bool ORIG>
 cudaError_t fused_step(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
@@ -249,7 +249,7 @@ cudaError_t fused_step(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
       }
       return launch_fused<L, S, 1, 1, 2, true, 2, ORIG>(d, g, ph, b);
     } else {
-      return launch_fused<L, S, 1, 1, 2, true, 1, ORIG>(d, g, ph, b);
+      return launch_fused<L, S, 1, 1, 2, true, 2, ORIG>(d, g, ph, b);
     }
   }
 }
