@@ -530,10 +530,10 @@ struct NoClosureSmem {
 
 // Shared memory of one tile and the choices that depend on its size.
 //  - Stage (PF): the next planes' populations of every collision thread
-//    (Q stress populations and its flow populations; chi apart, in its own
-//    type), copied with cp.async: FP32 and 16-bit storage, not with the
-//    learned closure.  NST buffers: the copies run NST - 1 planes ahead of
-//    the collision (three where the budget allows, else two).
+//    (Q stress populations and its flow populations, chi, and the 16-bit
+//    forms' FP32 arrays), copied with bulk tensor copies or cp.async: FP32
+//    and 16-bit storage.  NST buffers: the copies run NST - 1 planes ahead
+//    of the collision (three where the budget allows, else two).
 //  - The exchange arrays sAd / sPf are double-buffered by plane parity where
 //    the budget allows: plane m + 1 then writes the other copy while slower
 //    warps still read plane m's, and one barrier per plane suffices
@@ -553,7 +553,7 @@ struct TileCfg {
   static constexpr int NPP = Q + NFM;             // staged populations per thread
   static constexpr int BX = 32 * XN;              // stage columns of one warp
   static constexpr int CP = C == 6 ? 8 : 4;
-  static constexpr bool PF = (sizeof(S) == 4 || sizeof(S) == 2) && !CL;
+  static constexpr bool PF = sizeof(S) == 4 || sizeof(S) == 2;
   using CLS = typename std::conditional<CL, ClosureSmem<Sh::NG, C, NS>, NoClosureSmem>::type;
   static constexpr size_t kRing = sizeof(Vel<R, D>) * 4 * Sh::NE;
   // 16-bit forms: the FP32 rest stress population of the thread's
@@ -575,10 +575,11 @@ struct TileCfg {
   using WStage = typename std::conditional<V2, WStageV2, WStage0>::type;
   static constexpr size_t kStage1 = PF ? sizeof(WStage) * Sh::NCW : 0;
   static constexpr size_t kEx1 = 2 * sizeof(R) * CP * NS;
-  // dynamic shared memory: several rows per thread, a staged 2D tile or a
-  // staged 16-bit tile (whose stages fill the static 48 KB and leave no room
-  // for the double-buffered exchange or a third stage)
-  static constexpr bool kDynamic = XN > 1 || (PF && (D == 2 || V2));
+  // dynamic shared memory: several rows per thread, a staged 2D tile, a
+  // staged 16-bit tile or a staged tile with the learned closure (whose
+  // stages fill the static 48 KB and leave no room for the double-buffered
+  // exchange or a third stage)
+  static constexpr bool kDynamic = XN > 1 || (PF && (D == 2 || V2 || CL));
   static constexpr size_t kLimit = kDynamic ? (MINB >= 3 ? 72 : 110) * 1024 : 48 * 1024;
   static constexpr int NST =
       (PF && kRing + sizeof(CLS) + 3 * kStage1 + 2 * kEx1 <= kLimit) ? 3 : 2;
@@ -987,8 +988,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     }
     // Staged storage types keep this plane's values in stage buffer st
     // until the collision has used them (read there again rather than held
-    // in registers across the barrier); FP64 and the learned-closure kernel
-    // hold them in registers.
+    // in registers across the barrier); FP64 holds them in registers.
     R hv[PF ? 1 : Q], fo[PF ? 1 : NFM];
     R old = R(0);
     if (active) {

@@ -214,13 +214,13 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   dim3 grid(bx, by, nchunk);
   StageMaps tm;
   std::memset(&tm, 0, sizeof tm);
+  if constexpr (TileCfg<L, S, GX, TY, FW, false, XN, MINB>::PF) tm = stage_maps<L, S>(d, 32 * XN);
   if constexpr (std::is_same<S, float>::value && XN == 1 && !ORIG) {
     if (d.mlp) {  // learned closure (FP32 storage only); two blocks per SM
       if (d.walls) return launch_kernel<L, S, GX, TY, 2, true, FW, true, 1>(grid, d, g, ph, b, mchunk, tm);
       return launch_kernel<L, S, GX, TY, 2, false, FW, true, 1>(grid, d, g, ph, b, mchunk, tm);
     }
   }
-  if constexpr (TileCfg<L, S, GX, TY, FW, false, XN, MINB>::PF) tm = stage_maps<L, S>(d, 32 * XN);
   if (d.walls)
     return launch_kernel<L, S, GX, TY, MINB, true, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk, tm);
   return launch_kernel<L, S, GX, TY, MINB, false, FW, false, XN, ORIG>(grid, d, g, ph, b, mchunk, tm);
