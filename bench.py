@@ -279,9 +279,14 @@ def kernel_label(lattice: str, precision: str) -> str:
                 f"(128 nodes x 3 stress components per block, in-warp halo fill)")
     if precision == "fp32":
         return (f"k_step_fused<D3Q19,float,GX=1,TY=1,MINB=2,periodic,fill warps,XN=2> "
-                f"(64 nodes x 6 stress components + 4 halo fill warps per block)")
-    return (f"k_step_fused<D3Q19,{S},GX=1,TY=1,MINB={minb},periodic,fill warps> "
-            f"(32 nodes x 6 stress components + 4 halo fill warps per block)")
+                f"(64 nodes x 6 stress components + 7 halo fill warps per block, "
+                f"bulk tensor copies into the stage)")
+    if precision == "fp64":
+        return (f"k_step_fused<D3Q19,double,GX=1,TY=1,MINB=1,periodic,fill warps> "
+                f"(32 nodes x 6 stress components + 4 halo fill warps per block)")
+    return (f"k_step_fused<D3Q19,{S},GX=1,TY=1,MINB=2,periodic,fill warps,XN=2> "
+            f"(64 nodes x 6 stress components + 4 halo fill warps per block, "
+            f"bulk tensor copies into the stage)")
 
 
 def config_dict(args=None, note=""):

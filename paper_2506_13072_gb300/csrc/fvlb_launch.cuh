@@ -184,7 +184,7 @@ template <class L, class S, int GX, int TY, int MINB, bool WALLS, bool FW, bool 
           bool ORIG = false>
 cudaError_t launch_kernel(dim3 grid, const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                           const Bufs<S>& b, int mchunk, const StageMaps& tm) {
-  constexpr int NT = FusedShape<L, GX, TY, FW, XN>::NT;
+  constexpr int NT = FusedShape<L, GX, TY, FW, XN, fill_warps_max<S, XN>()>::NT;
   constexpr size_t dyn = TileCfg<L, S, GX, TY, FW, CL, XN, MINB>::kDynamicBytes;
   auto kern = k_step_fused<L, S, GX, TY, MINB, WALLS, FW, CL, XN, ORIG>;
   if constexpr (dyn > 0) {
@@ -229,9 +229,10 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
 // The fused step in the shape measured fastest on GB300 (256^3 D3Q19, 2048^2
 // D2Q9): 2D four 32-node groups x 3 components (384 threads, 2 blocks per
 // SM); 3D FP32 and 16-bit a 64-node row, each of the 6 component warps
-// taking its two 32-node halves in turn, + 4 halo fill warps (320 threads, 2
-// blocks per SM; a 64-register cap for 3 blocks per SM measured slower); 3D
-// FP64 and the learned closure one 32-node row.  ORIG: the original scheme's
+// taking its two 32-node halves in turn, + 7 (FP32) or 4 (16-bit) halo fill
+// warps (416 / 320 threads, 2 blocks per SM; a 64-register cap for 3 blocks
+// per SM measured slower); 3D FP64 and the learned closure one 32-node row
+// with 4 fill warps.  ORIG: the original scheme's
 // step (div tau_p from ph.fdiv in the body force, f^B off).
 template <class L, class S, bool ORIG>
 cudaError_t fused_step(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
