@@ -275,8 +275,13 @@ def kernel_label(lattice: str, precision: str) -> str:
          "fp16_dev_sr": "half_sr", "bf16_dev_sr": "bf16_sr"}[precision]
     minb = 1 if precision == "fp64" else 2
     if lattice == "d2q9":
-        return (f"k_step_fused<D2Q9,{S},GX=4,TY=1,MINB={minb},periodic> "
-                f"(128 nodes x 3 stress components per block, in-warp halo fill)")
+        if precision == "fp64":
+            return (f"k_step_fused<D2Q9,double,GX=4,TY=1,MINB=1,periodic> "
+                    f"(128 nodes x 3 stress components per block, in-warp halo fill)")
+        nfw = 5 if precision == "fp32" else 4
+        return (f"k_step_fused<D2Q9,{S},GX=4,TY=1,MINB=2,periodic,fill warps> "
+                f"(128 nodes x 3 stress components + {nfw} halo fill warps per block, "
+                f"bulk tensor copies into the stage)")
     if precision == "fp32":
         return (f"k_step_fused<D3Q19,float,GX=1,TY=1,MINB=2,periodic,fill warps,XN=2> "
                 f"(64 nodes x 6 stress components + 7 halo fill warps per block, "

@@ -501,12 +501,13 @@ __device__ __forceinline__ void on_component(int k, Fn&& fn) {
 // XN: nodes per collision thread along x; a collision warp covers XN rows
 // of 32 consecutive nodes of one plane, one after the other (with fill
 // warps only).  Up to four fill warps, each thread filling SPF ring slots.
-// Most fill warps of a tile: with the FP32 64-node rows one ring slot per
-// fill thread (7 warps, 72 registers: measured 3 % faster than 4 warps of
-// two slots each at 96 registers); 4 otherwise.
+// Most fill warps of a tile.  FP32: one ring slot per fill thread (3D
+// 64-node rows 7 warps at 72 registers, measured 3 % faster than 4 warps of
+// two slots each at 96; D2Q9 128-node tiles 5 warps at 56 registers, 7 %
+// faster than 4); 4 otherwise (the 16-bit forms spill with more).
 template <class S, int XN>
 __host__ __device__ constexpr int fill_warps_max() {
-  return (sizeof(S) == 4 && XN == 2) ? 7 : 4;
+  return sizeof(S) == 4 ? (XN == 2 ? 7 : 5) : 4;
 }
 
 template <class L, int GX, int TY, bool FW, int XN = 1, int NFWM = 4>

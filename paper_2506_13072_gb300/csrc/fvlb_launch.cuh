@@ -215,7 +215,7 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
   StageMaps tm;
   std::memset(&tm, 0, sizeof tm);
   if constexpr (TileCfg<L, S, GX, TY, FW, false, XN, MINB>::PF) tm = stage_maps<L, S>(d, 32 * XN);
-  if constexpr (std::is_same<S, float>::value && XN == 1 && !ORIG) {
+  if constexpr (std::is_same<S, float>::value && XN == 1 && !ORIG && (L::D == 3 || !FW)) {
     if (d.mlp) {  // learned closure (FP32 storage only); two blocks per SM
       if (d.walls) return launch_kernel<L, S, GX, TY, 2, true, FW, true, 1>(grid, d, g, ph, b, mchunk, tm);
       return launch_kernel<L, S, GX, TY, 2, false, FW, true, 1>(grid, d, g, ph, b, mchunk, tm);
@@ -227,8 +227,9 @@ cudaError_t launch_fused(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph
 }
 
 // The fused step in the shape measured fastest on GB300 (256^3 D3Q19, 2048^2
-// D2Q9): 2D four 32-node groups x 3 components (384 threads, 2 blocks per
-// SM); 3D FP32 and 16-bit a 64-node row, each of the 6 component warps
+// D2Q9): 2D four 32-node groups x 3 components + 5 (FP32) or 4 (16-bit) halo
+// fill warps (544 / 512 threads, 2 blocks per SM; FP64 and the learned
+// closure without fill warps, 384 threads); 3D FP32 and 16-bit a 64-node row, each of the 6 component warps
 // taking its two 32-node halves in turn, + 7 (FP32) or 4 (16-bit) halo fill
 // warps (416 / 320 threads, 2 blocks per SM; a 64-register cap for 3 blocks
 // per SM measured slower); 3D FP64 and the learned closure one 32-node row
@@ -239,9 +240,16 @@ cudaError_t fused_step(const StepDesc& d, const Grid& g, const Phys<RT<S>>& ph,
                        const Bufs<S>& b) {
   constexpr bool wide = sizeof(RT<S>) == 8;
   if constexpr (L::D == 2) {
-    // 4 groups x 3 components, ring filled by the collision threads
-    if constexpr (wide) return launch_fused<L, S, 4, 1, 1, false, 1, ORIG>(d, g, ph, b);
-    else return launch_fused<L, S, 4, 1, 2, false, 1, ORIG>(d, g, ph, b);
+    // 4 groups x 3 components; FP64 and the learned closure fill the ring
+    // in the collision threads, FP32 and 16-bit storage with fill warps
+    if constexpr (wide) {
+      return launch_fused<L, S, 4, 1, 1, false, 1, ORIG>(d, g, ph, b);
+    } else {
+      if constexpr (!ORIG) {
+        if (d.mlp) return launch_fused<L, S, 4, 1, 2, false, 1>(d, g, ph, b);
+      }
+      return launch_fused<L, S, 4, 1, 2, true, 1, ORIG>(d, g, ph, b);
+    }
   } else {
     if constexpr (wide) return launch_fused<L, S, 1, 1, 1, true, 1, ORIG>(d, g, ph, b);
     else if constexpr (sizeof(S) == 4) {
