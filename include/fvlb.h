@@ -51,7 +51,11 @@ enum {
   FVLB_ENOMEM = -2,    /* a device allocation failed */
   FVLB_ECUDA = -3,     /* a CUDA call failed */
   FVLB_EUNSTABLE = -4, /* the diagnostics found a non-finite value */
-  FVLB_ETIMEOUT = -5,  /* a bounded device wait ran out */
+  FVLB_ETIMEOUT = -5,  /* a bounded device wait ran out: a step kernel's staged
+                        * copies did not arrive within about 2 s; the state is
+                        * invalid until fvlb_init_fields / fvlb_load_state.
+                        * Reported by fvlb_fields, fvlb_reduce and
+                        * fvlb_status(h, 1). */
   FVLB_ESTATE = -6     /* call not allowed in the handle's current state */
 };
 
@@ -237,13 +241,16 @@ int fvlb_step(fvlb_t h, long n);
 int fvlb_set_check_interval(fvlb_t h, long every);
 
 /* Result of the periodic check: FVLB_OK, or FVLB_EUNSTABLE once a check has
- * found a non-finite value.  wait != 0 first waits for a check in flight. */
+ * found a non-finite value.  wait != 0 first waits for a check in flight,
+ * then synchronises the stream and returns FVLB_ETIMEOUT if a step kernel's
+ * bounded wait ran out. */
 int fvlb_status(fvlb_t h, int wait);
 
 /* Copy one field of the current state into host_out (FP64, layouts above),
  * synchronising the handle's stream.  count is the number of doubles the
  * buffer holds; if it is smaller than N * components, FVLB_EINVAL is
- * returned and nothing is written. */
+ * returned and nothing is written.  FVLB_ETIMEOUT (after the copy) if a step
+ * kernel's bounded wait ran out since the state was installed. */
 int fvlb_fields(fvlb_t h, int which, double *host_out, size_t count);
 
 /* FP64 diagnostics of the current state, reduced on the GPU in a fixed
@@ -254,7 +261,8 @@ int fvlb_fields(fvlb_t h, int which, double *host_out, size_t count);
  *   out[5]   PE = (1/M) sum_x tr(tau_p) / 2       (Sec. 3.4)
  *   out[6]   number of sites with a non-finite f, h or u
  *   out[7]   max_x |u|
- * Returns FVLB_EUNSTABLE (with out filled) if out[6] > 0. */
+ * Returns FVLB_EUNSTABLE (with out filled) if out[6] > 0, FVLB_ETIMEOUT (with
+ * out filled) if a step kernel's bounded wait ran out. */
 int fvlb_reduce(fvlb_t h, double out[8]);
 
 /* Conformation check of the current state, FP64, on the GPU, synchronising
