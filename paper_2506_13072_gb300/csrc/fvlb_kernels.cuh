@@ -393,7 +393,7 @@ __device__ __forceinline__ void collide_site(const Grid& g, const Phys<RT<S>>& p
           h0post[k] = post - R(kWx) * (ph.inv_tau_h * Ad[k] + src[k]);
         } else {
           S* q = b.h_out + (long long)(k * Q + j) * P + d;
-          hres[k] += post - Store<S>::st_r(q, post, Store<S>::sr ? lcg_next(rng) : 0u);
+          hres[k] -= Store<S>::st_d(q, post, Store<S>::sr ? lcg_next(rng) : 0u);
         }
       } else if constexpr (RS) {
         if (i != 0) {
@@ -1054,11 +1054,11 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if constexpr (V2) a = W.ext[0][c];
           else a = Store<S>::cvt(W.h[0][c]);
 #pragma unroll
-          for (int i = 1; i < Q; ++i) a += Store<S>::cvt(W.h[i][c]);
+          for (int i = 1; i < Q; ++i) a = Store<S>::acc(a, W.h[i][c]);
 #pragma unroll
           for (int j = 0; j < NFM; ++j) {
             const int i = k + j * C;
-            if (i != 0 && i < Q) psum += Store<S>::cvt(W.f[j][c]);
+            if (i != 0 && i < Q) psum = Store<S>::acc(psum, W.f[j][c]);
           }
           // (16-bit forms: the sum of the scaled deviations s_i, i != 0;
           // the collision adds the sum of e_i(U), i != 0, = 1.5 w_0 |U|^2)
@@ -1417,7 +1417,7 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
             } else {
               bool bnc;
               const uint32_t o = index(i, bnc);
-              hres += post - Store<S>::st_r(hout_k + o, post, Store<S>::sr ? lcg_next(rng) : 0u);
+              hres -= Store<S>::st_d(hout_k + o, post, Store<S>::sr ? lcg_next(rng) : 0u);
             }
           } else if constexpr (RS) {
             if (i != 0) {
@@ -1455,9 +1455,13 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
               const R Fi = ph.kf * (w3i * cF + wi * (R(9) * cF * cu - R(3) * Fu));
               const R fBi = fB_dir<L, R>(i, Ad, kB);
               R foi;
-              if constexpr (PF) foi = Store<S>::cvt(stage[st][warp].f[jj][col]);
-              else foi = fo[jj];
-              if constexpr (V2) foi = foi * R(1.0f / Store<S>::KF) + feq_u<L, R>(i, Us, UU);
+              if constexpr (PF && V2) {
+                foi = Store<S>::dev_add(stage[st][warp].f[jj][col], feq_u<L, R>(i, Us, UU));
+              } else {
+                if constexpr (PF) foi = Store<S>::cvt(stage[st][warp].f[jj][col]);
+                else foi = fo[jj];
+                if constexpr (V2) foi = foi * R(1.0f / Store<S>::KF) + feq_u<L, R>(i, Us, UU);
+              }
               const R post = foi - (foi - feq) * ph.inv_tau_f + fBi + Fi;
               bool bnc;
               const uint32_t o = index(i, bnc);

@@ -101,6 +101,36 @@ __device__ __forceinline__ unsigned short ld_l2_u16(const void* p) {
 template <class S>
 struct Store;
 
+// a + v for a 16-bit v, converted (exactly) and added in one mixed-precision
+// instruction: the same result as converting first and adding in FP32
+__device__ __forceinline__ float add_f16(float a, unsigned short v) {
+  float d;
+  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(v), "f"(a));
+  return d;
+}
+__device__ __forceinline__ float add_bf16(float a, unsigned short v) {
+  float d;
+  asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(v), "f"(a));
+  return d;
+}
+// v * w + a for 16-bit v and w, likewise (the product is exact in FP32)
+__device__ __forceinline__ float fma_f16(unsigned short v, unsigned short w, float a) {
+  float d;
+  asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(v), "h"(w), "f"(a));
+  return d;
+}
+// v - a for a 16-bit v, likewise
+__device__ __forceinline__ float sub_f16(unsigned short v, float a) {
+  float d;
+  asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(v), "f"(a));
+  return d;
+}
+__device__ __forceinline__ float sub_bf16(unsigned short v, float a) {
+  float d;
+  asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(v), "f"(a));
+  return d;
+}
+
 template <>
 struct Store<double> {
   using R = double;     // arithmetic
@@ -108,6 +138,7 @@ struct Store<double> {
   static constexpr bool V2 = false;  // no reference-based 16-bit layout (see below)
   __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double cvt(double v) { return v; }
+  __device__ static __forceinline__ double acc(double a, double v) { return a + v; }
   static constexpr bool sr = false;
   __device__ static __forceinline__ void st(double* p, double v, uint32_t) { *p = v; }
   __device__ static __forceinline__ double ld_l2(const double* p) {
@@ -124,6 +155,7 @@ struct Store<float> {
   static constexpr bool V2 = false;
   __device__ static __forceinline__ float ld(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float cvt(float v) { return v; }
+  __device__ static __forceinline__ float acc(float a, float v) { return a + v; }
   static constexpr bool sr = false;
   __device__ static __forceinline__ void st(float* p, float v, uint32_t) { *p = v; }
   __device__ static __forceinline__ float ld_l2(const float* p) {
@@ -144,6 +176,7 @@ struct Store<__half> {
     return __half2float(__ldg(p));
   }
   __device__ static __forceinline__ float cvt(__half v) { return __half2float(v); }
+  __device__ static __forceinline__ float acc(float a, __half v) { return add_f16(a, __half_as_ushort(v)); }
   __device__ static __forceinline__ void st(__half* p, float v, uint32_t) {
     *p = __float2half_rn(v);
   }
@@ -152,6 +185,16 @@ struct Store<__half> {
     const __half q = __float2half_rn(v);
     *p = q;
     return __half2float(q);
+  }
+  // v / KF + e (2^-12 is the FP16 number 0x0C00)
+  __device__ static __forceinline__ float dev_add(__half v, float e) {
+    return fma_f16(__half_as_ushort(v), 0x0C00, e);
+  }
+  // store, and return the stored value minus v (its rounding error)
+  __device__ static __forceinline__ float st_d(__half* p, float v, uint32_t) {
+    const __half q = __float2half_rn(v);
+    *p = q;
+    return sub_f16(__half_as_ushort(q), v);
   }
   __device__ static __forceinline__ float ld_l2(const __half* p) {
     return __half2float(__ushort_as_half(ld_l2_u16(p)));
@@ -169,6 +212,7 @@ struct Store<__nv_bfloat16> {
     return __bfloat162float(__ldg(p));
   }
   __device__ static __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __forceinline__ float acc(float a, __nv_bfloat16 v) { return add_bf16(a, __bfloat16_as_ushort(v)); }
   __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, uint32_t) {
     *p = __float2bfloat16_rn(v);
   }
@@ -176,6 +220,14 @@ struct Store<__nv_bfloat16> {
     const __nv_bfloat16 q = __float2bfloat16_rn(v);
     *p = q;
     return __bfloat162float(q);
+  }
+  __device__ static __forceinline__ float dev_add(__nv_bfloat16 v, float e) {  // KF = 1
+    return add_bf16(e, __bfloat16_as_ushort(v));
+  }
+  __device__ static __forceinline__ float st_d(__nv_bfloat16* p, float v, uint32_t) {
+    const __nv_bfloat16 q = __float2bfloat16_rn(v);
+    *p = q;
+    return sub_bf16(__bfloat16_as_ushort(q), v);
   }
   __device__ static __forceinline__ float ld_l2(const __nv_bfloat16* p) {
     return __uint_as_float((uint32_t)ld_l2_u16(p) << 16);
@@ -194,6 +246,8 @@ struct bf16_sr {
   unsigned short b;
 };
 
+static_assert(Store<__half>::KF == 4096.0f, "dev_add takes 1 / KF as the FP16 number 0x0C00 (2^-12)");
+
 template <>
 struct Store<half_sr> {
   using R = float;
@@ -207,6 +261,7 @@ struct Store<half_sr> {
   __device__ static __forceinline__ float cvt(half_sr v) {
     return __half2float(__ushort_as_half(v.b));
   }
+  __device__ static __forceinline__ float acc(float a, half_sr v) { return add_f16(a, v.b); }
   // r: 32 random bits.  Add r * ulp(|v|) in magnitude, then truncate.
   __device__ static __forceinline__ __half round(float v, uint32_t r) {
     const uint32_t bits = __float_as_uint(v);
@@ -225,6 +280,14 @@ struct Store<half_sr> {
     p->b = __half_as_ushort(q);
     return __half2float(q);
   }
+  __device__ static __forceinline__ float dev_add(half_sr v, float e) {
+    return fma_f16(v.b, 0x0C00, e);
+  }
+  __device__ static __forceinline__ float st_d(half_sr* p, float v, uint32_t r) {
+    const __half q = round(v, r);
+    p->b = __half_as_ushort(q);
+    return sub_f16(__half_as_ushort(q), v);
+  }
   __device__ static __forceinline__ float ld_l2(const half_sr* p) {
     return __half2float(__ushort_as_half(ld_l2_u16(p)));
   }
@@ -241,6 +304,7 @@ struct Store<bf16_sr> {
     return __uint_as_float((uint32_t)__ldg(&p->b) << 16);
   }
   __device__ static __forceinline__ float cvt(bf16_sr v) { return __uint_as_float((uint32_t)v.b << 16); }
+  __device__ static __forceinline__ float acc(float a, bf16_sr v) { return add_bf16(a, v.b); }
   // add 16 random bits below the kept 16 and truncate (sign-magnitude, so the
   // rounding is unbiased in magnitude and hence in value)
   __device__ static __forceinline__ void st(bf16_sr* p, float v, uint32_t r) {
@@ -255,6 +319,12 @@ struct Store<bf16_sr> {
     const uint32_t out = (exp == 0x7f800000u ? bits : bits + (r >> 16)) & 0xffff0000u;
     p->b = (unsigned short)(out >> 16);
     return __uint_as_float(out);
+  }
+  __device__ static __forceinline__ float dev_add(bf16_sr v, float e) {  // KF = 1
+    return add_bf16(e, v.b);
+  }
+  __device__ static __forceinline__ float st_d(bf16_sr* p, float v, uint32_t r) {
+    return st_r(p, v, r) - v;
   }
   __device__ static __forceinline__ float ld_l2(const bf16_sr* p) {
     return __uint_as_float((uint32_t)ld_l2_u16(p) << 16);
