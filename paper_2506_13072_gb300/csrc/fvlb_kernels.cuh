@@ -753,6 +753,84 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   // in-collision fill (memory phase of m + 1) writes plane m + 2 as well:
   // its slot (that of plane m - 2) was last read by the collision of plane
   // m - 1, which every warp finished before A(m).
+  // 16-bit storage with an even nx and no walls across x: each fill thread
+  // takes a pair of x-neighbouring nodes (x even, x + 1) of one ring row and
+  // loads each of their populations with one 4-byte load (and U as one
+  // 8-byte pair), half the loads and held registers of one slot per load.
+  // Pair px of row ey holds ring slots 2 px - 1 and 2 px (those in the row).
+  constexpr int PX = (EX + 2) / 2;
+  constexpr int NPR = Sh::EY * PX;
+  if constexpr (FW && sizeof(S) == 2) {
+    static_assert((EX & 1) == 0, "ring rows hold whole pairs");
+    if (filler && (nx & 1) == 0 && !wall_x && NPR <= NFW * 32) {
+      const int pp = tid - NCW * 32;
+      const int ey = pp / PX, px = pp - ey * PX;
+      const bool pact = pp < NPR;
+      int gx0 = x0 + 2 * px - 2;                  // even
+      gx0 = ((gx0 % nx) + nx) % nx;               // periodic in x (nx even: stays even)
+      int gy = (D == 3) ? y0 + ey - 1 : 0;
+      bool has = pact;
+      if (D == 3 && (gy < 0 || gy >= ny)) {
+        if (wall_y) has = false;
+        gy = ((gy % ny) + ny) % ny;
+      }
+      const int ea = ey * EX + 2 * px - 1;        // slot of node gx0 (px > 0)
+      const bool sa = pact && px > 0, sb = pact && 2 * px < EX;
+      uint32_t pv[Q];
+      float2 pu[V2 ? D : 1];
+      auto pload = [&](int mm) {
+        if (has && mm >= 0) {
+          const uint32_t s0 = (D == 3) ? ((uint32_t)mm * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx0
+                                       : (uint32_t)mm * (uint32_t)nx + (uint32_t)gx0;
+          const uint32_t* fw = reinterpret_cast<const uint32_t*>(b.f_in);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) pv[i] = __ldg(fw + (((uint32_t)i * P32 + s0) >> 1));
+          if constexpr (V2) {
+            const float* U = f_ext<L>(b.f_in, P);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+              pu[a] = __ldg(reinterpret_cast<const float2*>(U + ((uint32_t)a * P32 + s0)));
+          }
+        }
+      };
+      auto pstore = [&](int mm, int q) {
+        const bool ok = has && mm >= 0;
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+          if (n == 0 ? !sa : !sb) continue;
+          R fv[FQ];
+#pragma unroll
+          for (int i = 0; i < Q; ++i)
+            fv[i] = ok ? Store<S>::cvtb((unsigned short)(n ? pv[i] >> 16 : pv[i] & 0xffffu)) : R(0);
+          if constexpr (V2) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) fv[Q + a] = ok ? (n ? pu[a].y : pu[a].x) : R(0);
+          }
+          fill_store(ea + n, ok, mm, gx0 + n, gy, fv, q);
+        }
+      };
+      for (int q = m0 - 1; q <= m0 + 1; ++q) {
+        const int mm = plane_of(q);
+        pload(mm);
+        pstore(mm, q);
+      }
+      int mq = plane_of(m0 + 2);
+      if (m0 + 2 <= m1) pload(mq);
+      __syncthreads();
+      for (int m = m0; m < m1; ++m) {
+        __syncthreads();               // A: collision loads of plane m done
+        if constexpr (CL) __syncthreads();  // C: learned closure done
+        if (m + 2 <= m1) {             // overlaps the collision of plane m
+          pstore(mq, m + 2);
+          mq = plane_of(m + 3);
+          if (m + 3 <= m1) pload(mq);
+        }
+        if constexpr (NBUF == 1) __syncthreads();  // B
+      }
+      if constexpr (NBUF == 2) __syncthreads();  // tile done (shared memory reuse)
+      return;
+    }
+  }
   if (FW && filler) {
     // ---------------- fill warps ---------------------------------------------
     // Each thread fills the ring slots e0 + t * 32 NFW, t < SPF; their node
