@@ -510,6 +510,12 @@ __host__ __device__ constexpr int fill_warps_max() {
   return sizeof(S) == 4 ? (XN == 2 ? 7 : 5) : 4;
 }
 
+// Fill warps that take x-neighbouring node pairs (see fused_tile).
+template <class S, int XN>
+__host__ __device__ constexpr bool fill_pairs() {
+  return sizeof(S) == 2;
+}
+
 template <class L, int GX, int TY, bool FW, int XN = 1, int NFWM = 4>
 struct FusedShape {
   static constexpr int NG = GX * TY;              // groups of 32 x XN nodes per plane tile
@@ -753,15 +759,18 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
   // in-collision fill (memory phase of m + 1) writes plane m + 2 as well:
   // its slot (that of plane m - 2) was last read by the collision of plane
   // m - 1, which every warp finished before A(m).
-  // 16-bit storage with an even nx and no walls across x: each fill thread
+  // With an even nx and no walls across x (and fill_pairs), each fill thread
   // takes a pair of x-neighbouring nodes (x even, x + 1) of one ring row and
-  // loads each of their populations with one 4-byte load (and U as one
-  // 8-byte pair), half the loads and held registers of one slot per load.
-  // Pair px of row ey holds ring slots 2 px - 1 and 2 px (those in the row).
+  // loads each of their populations with one load of two elements (and U as
+  // one 8-byte pair), half the loads and held registers of one slot per
+  // load.  Pair px of row ey holds ring slots 2 px - 1 and 2 px (those in
+  // the row).
+  constexpr bool PAIRFILL = fill_pairs<S, XN>() && sizeof(S) <= 4;
   constexpr int PX = (EX + 2) / 2;
   constexpr int NPR = Sh::EY * PX;
-  if constexpr (FW && sizeof(S) == 2) {
+  if constexpr (FW && PAIRFILL) {
     static_assert((EX & 1) == 0, "ring rows hold whole pairs");
+    using PT = typename std::conditional<sizeof(S) == 2, uint32_t, float2>::type;
     if (filler && (nx & 1) == 0 && !wall_x && NPR <= NFW * 32) {
       const int pp = tid - NCW * 32;
       const int ey = pp / PX, px = pp - ey * PX;
@@ -776,13 +785,13 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
       }
       const int ea = ey * EX + 2 * px - 1;        // slot of node gx0 (px > 0)
       const bool sa = pact && px > 0, sb = pact && 2 * px < EX;
-      uint32_t pv[Q];
+      PT pv[Q];
       float2 pu[V2 ? D : 1];
       auto pload = [&](int mm) {
         if (has && mm >= 0) {
           const uint32_t s0 = (D == 3) ? ((uint32_t)mm * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx0
                                        : (uint32_t)mm * (uint32_t)nx + (uint32_t)gx0;
-          const uint32_t* fw = reinterpret_cast<const uint32_t*>(b.f_in);
+          const PT* fw = reinterpret_cast<const PT*>(b.f_in);
 #pragma unroll
           for (int i = 0; i < Q; ++i) pv[i] = __ldg(fw + (((uint32_t)i * P32 + s0) >> 1));
           if constexpr (V2) {
@@ -800,8 +809,12 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
           if (n == 0 ? !sa : !sb) continue;
           R fv[FQ];
 #pragma unroll
-          for (int i = 0; i < Q; ++i)
-            fv[i] = ok ? Store<S>::cvtb((unsigned short)(n ? pv[i] >> 16 : pv[i] & 0xffffu)) : R(0);
+          for (int i = 0; i < Q; ++i) {
+            if constexpr (sizeof(S) == 2)
+              fv[i] = ok ? Store<S>::cvtb((unsigned short)(n ? pv[i] >> 16 : pv[i] & 0xffffu)) : R(0);
+            else
+              fv[i] = ok ? (n ? pv[i].y : pv[i].x) : R(0);
+          }
           if constexpr (V2) {
 #pragma unroll
             for (int a = 0; a < D; ++a) fv[Q + a] = ok ? (n ? pu[a].y : pu[a].x) : R(0);
