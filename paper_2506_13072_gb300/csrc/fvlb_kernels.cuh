@@ -729,6 +729,51 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
     if constexpr (D == 3) t.v[3] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];  // |u|^2
     ring[slot(q)][e] = t;
   };
+  // fill_store from the raw 16-bit populations sb and FP32 U (16-bit forms):
+  // the momentum sums take each population with one mixed-precision add or
+  // subtract, the accumulator's sign tracked at compile time (f - v = -(v - f)
+  // exactly), so the sums equal those of the converted values
+  auto fill_store_bits = [&](int e, bool ok, int mm, int gx, int gy,
+                             const unsigned short (&sb)[Q], const R (&Ub)[D], int q) {
+    R u[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = R(0);
+    if constexpr (V2 && sizeof(S) == 2) {
+      if (ok) {
+        R F[3];
+        body_force<L, R>(ph, gx, D == 3 ? gy : mm, F);
+        if constexpr (ORIG) {
+          const uint32_t sf = (D == 3) ? ((uint32_t)mm * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx
+                                       : (uint32_t)mm * (uint32_t)nx + (uint32_t)gx;
+#pragma unroll
+          for (int a = 0; a < D; ++a) F[a] += ph.fdiv[(uint32_t)a * P32 + sf];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          R v = R(0);
+          bool neg = false;   // v = -(momentum sum) while set
+#pragma unroll
+          for (int i = 1; i < Q; ++i) {
+            const int c = cc<L>(i, a);
+            if (c == 0) continue;
+            if ((c == 1) != neg) {
+              v = Store<S>::accb(v, sb[i]);
+            } else {
+              v = Store<S>::subb(sb[i], v);
+              neg = !neg;
+            }
+          }
+          const R m = neg ? -v : v;
+          u[a] = m * R(1.0f / Store<S>::KF) + Ub[a] + R(0.5) * F[a];
+        }
+      }
+    }
+    Vel<R, D> t;
+#pragma unroll
+    for (int a = 0; a < (D == 3 ? 4 : 2); ++a) t.v[a] = a < D ? u[a] : R(0);
+    if constexpr (D == 3) t.v[3] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];  // |u|^2
+    ring[slot(q)][e] = t;
+  };
   auto fill_load = [&](bool ok, int mm, int gx, int gy, R (&fv)[FQ]) {
     if (ok) {
       // 32-bit offsets (Q * pitch < 2^32)
@@ -807,6 +852,16 @@ __device__ __forceinline__ void fused_tile(const Grid& g, const Phys<RT<S>>& ph,
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
           if (n == 0 ? !sa : !sb) continue;
+          if constexpr (sizeof(S) == 2 && V2) {
+            unsigned short hb[Q];
+            R Ub[D];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) hb[i] = (unsigned short)(n ? pv[i] >> 16 : pv[i] & 0xffffu);
+#pragma unroll
+            for (int a = 0; a < D; ++a) Ub[a] = n ? pu[a].y : pu[a].x;
+            fill_store_bits(ea + n, ok, mm, gx0 + n, gy, hb, Ub, q);
+            continue;
+          }
           R fv[FQ];
 #pragma unroll
           for (int i = 0; i < Q; ++i) {

@@ -177,6 +177,8 @@ struct Store<__half> {
   }
   __device__ static __forceinline__ float cvt(__half v) { return __half2float(v); }
   __device__ static __forceinline__ float cvtb(unsigned short b) { return __half2float(__ushort_as_half(b)); }
+  __device__ static __forceinline__ float accb(float a, unsigned short b) { return add_f16(a, b); }
+  __device__ static __forceinline__ float subb(unsigned short b, float a) { return sub_f16(b, a); }
   __device__ static __forceinline__ float acc(float a, __half v) { return add_f16(a, __half_as_ushort(v)); }
   __device__ static __forceinline__ void st(__half* p, float v, uint32_t) {
     *p = __float2half_rn(v);
@@ -214,6 +216,8 @@ struct Store<__nv_bfloat16> {
   }
   __device__ static __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __forceinline__ float cvtb(unsigned short b) { return __uint_as_float((uint32_t)b << 16); }
+  __device__ static __forceinline__ float accb(float a, unsigned short b) { return add_bf16(a, b); }
+  __device__ static __forceinline__ float subb(unsigned short b, float a) { return sub_bf16(b, a); }
   __device__ static __forceinline__ float acc(float a, __nv_bfloat16 v) { return add_bf16(a, __bfloat16_as_ushort(v)); }
   __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, uint32_t) {
     *p = __float2bfloat16_rn(v);
@@ -264,6 +268,8 @@ struct Store<half_sr> {
     return __half2float(__ushort_as_half(v.b));
   }
   __device__ static __forceinline__ float cvtb(unsigned short b) { return __half2float(__ushort_as_half(b)); }
+  __device__ static __forceinline__ float accb(float a, unsigned short b) { return add_f16(a, b); }
+  __device__ static __forceinline__ float subb(unsigned short b, float a) { return sub_f16(b, a); }
   __device__ static __forceinline__ float acc(float a, half_sr v) { return add_f16(a, v.b); }
   // r: 32 random bits.  Add r * ulp(|v|) in magnitude, then truncate.
   __device__ static __forceinline__ __half round(float v, uint32_t r) {
@@ -308,6 +314,8 @@ struct Store<bf16_sr> {
   }
   __device__ static __forceinline__ float cvt(bf16_sr v) { return __uint_as_float((uint32_t)v.b << 16); }
   __device__ static __forceinline__ float cvtb(unsigned short b) { return __uint_as_float((uint32_t)b << 16); }
+  __device__ static __forceinline__ float accb(float a, unsigned short b) { return add_bf16(a, b); }
+  __device__ static __forceinline__ float subb(unsigned short b, float a) { return sub_bf16(b, a); }
   __device__ static __forceinline__ float acc(float a, bf16_sr v) { return add_bf16(a, v.b); }
   // add 16 random bits below the kept 16 and truncate (sign-magnitude, so the
   // rounding is unbiased in magnitude and hence in value)
